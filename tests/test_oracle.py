@@ -1,0 +1,253 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: the paper's worked examples
+(tests/golden), closed-form values and interaction counts derived by hand
+from the rules, an independent brute-force enumeration of every reduction
+order (tests/bruteforce.py), and the invariants of Sec. 2.1 / Sec. 2.2.
+"""
+import json
+import os
+
+import pytest
+
+import workloads as W
+from tests import bruteforce
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+R = W.ARITH_RULES
+RULE = {name: i for i, name in enumerate(W.ARITH_RULE_NAMES)}
+
+
+def golden():
+    with open(os.path.join(HERE, "golden", "paper_examples.jsonl")) as f:
+        return [json.loads(line) for line in f if line.strip()]
+
+
+# --- closed forms, written from the rules by hand ---------------------------
+
+def fib(n):
+    a, b = 0, 1
+    for _ in range(n):
+        a, b = b, a + b
+    return a
+
+
+def ack(m, n):
+    # Textbook closed forms for m <= 3 (checked against the recursive
+    # definition on small arguments in test_ack_closed_forms).
+    return [n + 1, n + 2, 2 * n + 3, 2 ** (n + 3) - 3][m]
+
+
+def ack_rec(m, n):
+    if m == 0:
+        return n + 1
+    if n == 0:
+        return ack_rec(m - 1, 1)
+    return ack_rec(m - 1, ack_rec(m, n - 1))
+
+
+def count_mul(m, n):
+    # Mul><Z once, Era over the copy of n (n+1), and per Mul><S step k
+    # (k = 0..m-1): itself, Dup over n (n+1), and Add over k*n (k*n+1).
+    return 1 + (n + 1) + sum(1 + (n + 1) + (k * n + 1) for k in range(m))
+
+
+def count_ack(m, n):
+    # A><Z: 1.  A><S then A2><Z: 2 + C(m-1, 1).  A><S then A2><S:
+    # 2 + the Dup of m-1 (m steps) + C(m, n-1) + C(m-1, ack(m, n-1)).
+    # Tables are filled bottom-up (the recursion is too deep for Python).
+    tab = {0: None}
+
+    def c(mm, nn):
+        if mm == 0:
+            return 1
+        row = tab.setdefault(mm, [])
+        while len(row) <= nn:
+            k = len(row)
+            if k == 0:
+                row.append(2 + c(mm - 1, 1))
+            else:
+                row.append(2 + mm + row[k - 1] + c(mm - 1, ack(mm, k - 1)))
+        return row[nn]
+
+    return c(m, n)
+
+
+def count_fib(n):
+    # Fib><Z: 1.  Fib><S + Fib2><Z: 2.  Fib><S + Fib2><S: 2 + Dup of k=n-2
+    # (k+1) + fib(k+1) and fib(k) subcomputations + Add over fib(k+1).
+    c = [1, 2]
+    for k in range(0, n - 1):
+        c.append(2 + (k + 1) + c[k + 1] + c[k] + fib(k + 1) + 1)
+    return c[n]
+
+
+# --- the paper's worked examples ---------------------------------------------
+
+@pytest.mark.parametrize("case", golden(), ids=lambda c: c["id"])
+def test_paper_examples(oracle, case):
+    e = case["expect"]
+    r = oracle.run(case["rules"], case["net"])[0]
+    assert r["status"] == "ok", r
+    assert r["result"] == e["result"]
+    assert r["interactions"] == e["interactions"]
+    if "nat" in e:
+        assert r["nat"] == e["nat"]
+    if "live" in e:
+        assert r["live"] == e["live"]
+    rr = oracle.run(case["rules"], case["net"], mode="rounds")[0]
+    assert rr.get("rounds", []) == e["rounds"]
+
+
+# --- closed forms --------------------------------------------------------------
+
+def test_add_values_and_counts(oracle):
+    cases = [(m, n) for m in range(0, 9) for n in range(0, 9)] + [(256, 0), (0, 256), (200, 57)]
+    res = oracle.run(R, [W.add_net(m, n) for m, n in cases], quiet=True)
+    for (m, n), r in zip(cases, res):
+        assert r["status"] == "ok"
+        assert r["nat"] == m + n
+        assert r["interactions"] == m + 1
+        assert r["per_rule"][RULE["Add><S"]] == m
+        assert r["per_rule"][RULE["Add><Z"]] == 1
+        assert r["live"] == m + n + 1          # garbage-free: exactly S^(m+n) Z remains
+
+
+def test_mul_values_counts_and_histogram(oracle):
+    cases = [(m, n) for m in range(0, 7) for n in range(0, 7)] + [(12, 9), (64, 64)]
+    res = oracle.run(R, [W.mul_net(m, n) for m, n in cases], quiet=True)
+    for (m, n), r in zip(cases, res):
+        assert r["status"] == "ok"
+        assert r["nat"] == m * n
+        assert r["interactions"] == count_mul(m, n)
+        h = r["per_rule"]
+        assert h[RULE["Mul><S"]] == m and h[RULE["Mul><Z"]] == 1
+        assert h[RULE["Dup><S"]] == m * n and h[RULE["Dup><Z"]] == m
+        assert h[RULE["Era><S"]] == n and h[RULE["Era><Z"]] == 1
+        assert h[RULE["Add><S"]] == n * m * (m - 1) // 2 and h[RULE["Add><Z"]] == m
+        assert r["live"] == m * n + 1
+
+
+def test_ackermann_values_and_counts(oracle):
+    cases = [(a, b) for a in range(0, 3) for b in range(0, 6)] + [(3, b) for b in range(0, 6)]
+    res = oracle.run(R, [W.ack_net(a, b) for a, b in cases], quiet=True)
+    for (a, b), r in zip(cases, res):
+        assert r["status"] == "ok"
+        assert r["nat"] == ack(a, b)
+        assert r["interactions"] == count_ack(a, b)
+        assert r["live"] == ack(a, b) + 1
+    assert count_ack(3, 7) == 1388937 and ack(3, 8) == 2045
+
+
+def test_ack_closed_forms():
+    for m in range(4):
+        for n in range(5 if m == 3 else 12):
+            assert ack(m, n) == ack_rec(m, n)
+
+
+def test_fibonacci_values_and_counts(oracle):
+    ns = list(range(0, 18))
+    res = oracle.run(R, [W.fib_net(n) for n in ns], quiet=True)
+    for n, r in zip(ns, res):
+        assert r["status"] == "ok"
+        assert r["nat"] == fib(n)
+        assert r["interactions"] == count_fib(n)
+        assert r["live"] == fib(n) + 1
+    assert fib(20) == 6765 and count_fib(20) == 138336
+
+
+def test_pred(oracle):
+    res = oracle.run(R, [W.pred_net(n) for n in range(5)])
+    for n, r in enumerate(res):
+        assert r["nat"] == max(0, n - 1) and r["interactions"] == 1
+
+
+# --- invariants: uniform confluence (Sec. 2.1) and Theorem 1 (Sec. 2.2) -------
+
+SMALL = [W.add_net(5, 3), W.mul_net(4, 3), W.ack_net(2, 2), W.ack_net(3, 1), W.fib_net(9),
+         "< r | Add(y, r) = S(Z), Add(S(Z), y) = Z >",
+         "< a, b | Dup(a, b) = S(S(Z)) >"]
+
+
+def test_every_schedule_gives_the_same_result(oracle):
+    ref = oracle.run(R, SMALL)
+    for mode, seed in [("fifo", 1), ("rounds", 1), ("random", 1), ("random", 7), ("random", 12345)]:
+        got = oracle.run(R, SMALL, mode=mode, seed=seed)
+        for a, b in zip(ref, got):
+            assert (a["result"], a["interactions"], a["per_rule"], a["live"]) == \
+                   (b["result"], b["interactions"], b["per_rule"], b["live"]), mode
+
+
+def test_deferring_sub_and_col_changes_nothing(oracle):
+    # Theorem 1: int/com first, sub/col at the end == interleaving them.
+    ref = oracle.run(R, SMALL)
+    eager = oracle.run(R, SMALL, eager=True)
+    for a, b in zip(ref, eager):
+        assert (a["result"], a["interactions"]) == (b["result"], b["interactions"])
+
+
+def test_rounds_profile_sums_to_interactions(oracle):
+    res = oracle.run(R, [W.fib_net(12), W.ack_net(3, 3), W.mul_net(9, 7)], mode="rounds")
+    for r in res:
+        assert sum(r["rounds"]) == r["interactions"]
+        assert len(r["live_rounds"]) == len(r["rounds"])
+        assert max(r["live_rounds"]) <= r["peak_live"]
+    # Add is sequential: one active pair per round.
+    r = oracle.run(R, W.add_net(20, 5), mode="rounds")[0]
+    assert r["rounds"] == [1] * 21
+
+
+BRUTE = [W.add_net(2, 1), W.mul_net(1, 2), W.mul_net(2, 2), W.ack_net(1, 1), W.ack_net(2, 1),
+         W.fib_net(3), W.fib_net(4), "< a, b | Dup(a, b) = S(S(Z)) >",
+         "< r | Add(y, r) = S(Z), Add(S(Z), y) = Z >"]
+
+
+@pytest.mark.parametrize("net", BRUTE)
+def test_bruteforce_all_orders(oracle, net):
+    bf = bruteforce.explore(R, net)
+    assert bf["consistent"], "two maximal reduction paths of different length"
+    assert bf["min"] == bf["max"]
+    assert len(bf["finals"]) == 1, bf["finals"]
+    (text, residual), = bf["finals"]
+    r = oracle.run(R, net)[0]
+    assert r["result"] == text and r["residual_eqs"] == residual
+    assert r["interactions"] == bf["min"]
+
+
+# --- the linker cases of Sec. 3.6 and degenerate nets ---------------------------
+
+def test_chain_of_names_resolves_to_one_pair(oracle):
+    rules = "Alpha = Beta -> ;\n"
+    for k in range(0, 6):
+        chain = ", ".join([f"x{i} = x{i + 1}" for i in range(k)])
+        net = f"< | Alpha = x0{', ' + chain if chain else ''}, x{k} = Beta >"
+        r = oracle.run(rules, net, mode="rounds")[0]
+        assert r["interactions"] == 1 and r["rounds"] == [1] and r["live"] == 0
+
+
+def test_vicious_circles(oracle):
+    r = oracle.run(R, "< | x = y, y = x >")[0]
+    assert r["status"] == "ok" and r["interactions"] == 0 and r["residual_eqs"] == 1
+    r = oracle.run(R, "< | x = S(y), y = S(x) >")[0]
+    assert r["residual_eqs"] == 1 and r["residual_agents"] == 2
+
+
+def test_empty_and_trivial_nets(oracle):
+    assert oracle.run(R, "< | >")[0]["result"] == ""
+    r = oracle.run(R, "< r, s | r = s >")[0]
+    assert r["result"] == "x0, x0" and r["interactions"] == 0
+    r = oracle.run(R, "< S(Z) | >")[0]
+    assert r["nat"] == 1
+
+
+# --- errors ---------------------------------------------------------------------
+
+def test_errors(oracle):
+    foo = "Foo(x) = Bar -> x = Bar;\n"
+    assert oracle.run(foo, "< r | Foo(r) = Baz >")[0]["status"] == "PARSE"
+    assert oracle.run(foo + "Baz = Bar -> ;\n", "< r | Foo(r) = Baz >")[0]["status"] == "NO_RULE"
+    assert oracle.run("Foo(x) = Bar -> ;\n", "< | >")[0].get("rules") == "LINEARITY"
+    assert oracle.run(R, "< r | Add(x, r) = S(x), x = Z >")[0]["status"] == "LINEARITY"
+    bad = oracle.run("Foo(x) = Bar -> x = y;\n", "< | >")[0]
+    assert bad.get("rules") == "LINEARITY"
+    assert oracle.run(R, W.fib_net(10), max_interactions=100)[0]["status"] == "STEP_LIMIT"
