@@ -1,0 +1,206 @@
+/*
+ * inet.h -- C ABI of the GB300 interaction-net evaluator.
+ *
+ * The library evaluates configurations < t.. | Delta > of the lightweight
+ * interaction calculus (Sec. 2.2) under a set of interaction rules
+ * alpha(x..) = beta(y..) -> Theta.  The hot loop is the data-parallel
+ * reduction step of Sec. 3.3-3.5: every active pair of the current frontier
+ * is rewritten by its rule (->int), the new agents and names are allocated,
+ * and the new equations are linked (->com, with ->sub of auxiliary ports at
+ * instantiation), until no active pair remains (Sec. 3.6, evaluate()).
+ * ->col and the remaining ->sub steps are applied at readback (Theorem 1).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an inet_status: INET_OK (0) or a negative code.
+ *     Errors never abort the process; inet_last_error() gives a message.
+ *   - The caller owns every host buffer it passes; the library copies what
+ *     it needs during the call and keeps no caller pointer, except for the
+ *     device workspace given to inet_attach_workspace().
+ *   - Device work is ordered on the context's CUDA stream.  inet_reduce()
+ *     returns when the requested reduction has finished on the device.
+ *   - A context is used by one host thread at a time.
+ *   - Text syntax: agent symbols start with an upper-case letter, names
+ *     with a lower-case letter (Sec. 3.3).  A rule is
+ *       Alpha(x1, .., xn) = Beta(y1, .., ym) -> t1 = u1, .., tk = uk;
+ *     (an empty right-hand side is written "-> ;") and a net is
+ *       < t1, .., tp | u1 = v1, .., uq = vq >
+ *     '#' starts a comment.  Arity is fixed by first use (at most 3).
+ */
+#ifndef INET_H
+#define INET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct inet_ctx inet_ctx;
+typedef int32_t inet_status;
+
+enum {
+  INET_OK = 0,
+  INET_ERR_INVALID_ARG = -1, /* bad pointer, size, id or option; truncated readback */
+  INET_ERR_PARSE = -2,       /* malformed text, unknown symbol, arity mismatch */
+  INET_ERR_LINEARITY = -3,   /* a name occurs more than twice (Sec. 2.2, Configurations),
+                                or a rule name is not bound linearly */
+  INET_ERR_NO_RULE = -4,     /* an active pair has no rule (premise of the
+                                Proposition on the correctness of evaluate(), Sec. 3.6) */
+  INET_ERR_ARENA_FULL = -5,  /* agent, name, frontier or net capacity exhausted */
+  INET_ERR_STEP_LIMIT = -6,  /* inet_reduce_opts.max_steps reached; resumable */
+  INET_ERR_TIMEOUT = -7,     /* a device-side wait gave up (persistent form) */
+  INET_ERR_CUDA = -8,        /* a CUDA runtime call failed */
+  INET_ERR_NO_DEVICE = -9,   /* operation needs a GPU; context is host-only */
+  INET_ERR_STATE = -10       /* call out of order, or context poisoned by an
+                                earlier ARENA_FULL / TIMEOUT / CUDA error */
+};
+
+/* Capacities of the device arena.  Zero fields take defaults. */
+typedef struct inet_arena_cfg {
+  uint64_t max_agents; /* agent slots, 16 bytes each (default 1<<22) */
+  uint64_t max_vars;   /* name slots, 4 bytes each (default 1<<22) */
+  uint64_t max_pairs;  /* frontier capacity, 8 bytes per pair, two buffers (default 1<<21) */
+  uint32_t max_nets;   /* independent nets held at once (default 1<<16) */
+  uint32_t reserved;
+} inet_arena_cfg;
+
+/* How the step loop of Sec. 3.6 (evaluate()) is driven. */
+enum {
+  INET_MODE_PLAIN = 0,      /* host loop: one kernel launch and one 16-byte
+                               device-to-host read of the frontier size per step */
+  INET_MODE_GRAPH = 1,      /* the step kernel inside a CUDA graph with a
+                               conditional WHILE node; no host round trip */
+  INET_MODE_PERSISTENT = 2  /* one cooperative launch; a grid barrier between
+                               steps; narrow frontiers run on one block */
+};
+
+typedef struct inet_reduce_opts {
+  int32_t mode;          /* INET_MODE_* */
+  int32_t block;         /* threads per block, multiple of 32 in [64, 1024]; 0 = 256 */
+  int32_t grid;          /* blocks for GRAPH / PERSISTENT; 0 = automatic */
+  int32_t solo_max;      /* PERSISTENT: frontier sizes <= solo_max run on block 0
+                            alone; 0 = automatic, < 0 = never */
+  uint64_t max_steps;    /* stop after this many steps of this call (0 = no limit);
+                            returns INET_ERR_STEP_LIMIT, state stays resumable */
+  uint64_t timeout_ns;   /* limit of any device-side wait (0 = 10 s) */
+  int32_t trace;         /* 1 = record frontier size and live agents per step */
+  int32_t reserved;
+} inet_reduce_opts;
+
+#define INET_MAX_RULES 64
+
+typedef struct inet_reduce_stats {
+  uint64_t interactions;        /* ->int steps performed by this call */
+  uint64_t steps;               /* loop iterations of this call */
+  uint64_t max_frontier;        /* largest frontier seen in this call */
+  int64_t  live_agents;         /* agents alive after the call (all nets) */
+  int64_t  peak_live_agents;    /* max of live agents at step boundaries */
+  uint64_t pending_pairs;       /* active pairs left (non-zero after STEP_LIMIT) */
+  double   device_ms;           /* device time of the step loop (CUDA events) */
+  uint32_t n_rules;
+  uint32_t launches;            /* kernel launches of this call (a graph's
+                                   body counts once per step) */
+  uint64_t per_rule[INET_MAX_RULES]; /* interactions by rule, rule-text order */
+} inet_reduce_stats;
+
+typedef struct inet_net_stats {
+  int32_t  status;        /* INET_OK or the first error of this net */
+  int32_t  reduced;       /* 1 once the net has no pending pair */
+  uint64_t interactions;  /* ->int steps of this net so far */
+  uint64_t pending_pairs; /* active pairs of this net in the frontier */
+  int64_t  live_agents;   /* agents of this net alive (readback snapshot) */
+  int64_t  residual_agents; /* live agents not reachable from the interface */
+} inet_net_stats;
+
+/* Shape of one compiled rule (for byte accounting and tools). */
+typedef struct inet_rule_desc {
+  char name[64];        /* "Alpha><Beta" */
+  int32_t arity_alpha;  /* auxiliary ports of the two LHS agents */
+  int32_t arity_beta;
+  int32_t n_new;        /* agents of Theta */
+  int32_t new_ports;    /* sum of the arities of the agents of Theta */
+  int32_t n_fresh;      /* bound names of Theta joining two auxiliary ports */
+  int32_t n_link;       /* equations of Theta' linked after instantiation */
+} inet_rule_desc;
+
+/* Number of rules of the loaded rule set. */
+inet_status inet_rule_count(const inet_ctx* ctx, int32_t* n_out);
+
+/* Shape of rule `rule` (text order, 0-based). */
+inet_status inet_rule_info(const inet_ctx* ctx, int32_t rule, inet_rule_desc* out);
+
+/* Workspace bytes the given capacities need (cfg may be NULL). */
+inet_status inet_workspace_bytes(const inet_arena_cfg* cfg, size_t* bytes_out);
+
+/* Creates a context on CUDA device `device` (device < 0: host-only context,
+ * which parses and loads but cannot reduce: INET_ERR_NO_DEVICE).  `stream`
+ * is a cudaStream_t or NULL for a stream the context creates.  `cfg` may be
+ * NULL.  The device workspace is allocated at the first load unless one is
+ * attached first. */
+inet_status inet_create(inet_ctx** out, int device, void* stream, const inet_arena_cfg* cfg);
+
+/* Uses caller-owned device memory (e.g. from a PyTorch allocator) as the
+ * workspace.  `bytes` must be >= inet_workspace_bytes() for the context's
+ * capacities and `dptr` 256-byte aligned.  The memory must stay valid until
+ * inet_destroy().  Must be called before the first load. */
+inet_status inet_attach_workspace(inet_ctx* ctx, void* dptr, size_t bytes);
+
+void inet_destroy(inet_ctx* ctx);
+
+/* Parses and compiles a rule set (Sec. 2.2, Interaction Rules): checks
+ * arities and linearity (every LHS name occurs once in Theta, every other
+ * name twice), stores each rule under the unordered pair {alpha, beta}
+ * (t = s is s = t, Sec. 2.2) and compiles Theta into an instantiation
+ * template.  Replaces any earlier rule set; allowed only while no net is
+ * loaded. */
+inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len);
+
+/* Parses one configuration < t.. | Delta > (Sec. 2.2, Configurations),
+ * checks that every name occurs at most twice, flattens nested terms into
+ * agent records (a subterm's principal port is linked to its parent's
+ * auxiliary port), applies ->com to the initial equations, and stages the
+ * result for the device.  Returns the net id. */
+inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* net_id_out);
+
+/* Adds the active pairs of the listed nets (which must not have been
+ * reduced yet; n may be 0) to the frontier and runs the reduction loop of
+ * Sec. 3.6 until no active pair remains in the whole context, an error
+ * occurs, or opts->max_steps steps have run.  opts and stats may be NULL.
+ * Per-net errors (NO_RULE) do not stop other nets; the first error is
+ * returned. */
+inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
+                        const inet_reduce_opts* opts, inet_reduce_stats* stats);
+
+/* Writes the net's interface after ->col and ->sub (Sec. 2.2; Theorem 1),
+ * terms left to right, names renamed x0, x1, .. in order of first
+ * occurrence, as a NUL-terminated string.  If cap is too small returns
+ * INET_ERR_INVALID_ARG with *needed_out set (needed_out may be NULL). */
+inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, size_t* needed_out);
+
+/* If the net's interface is a single numeral S^k(Z), stores k.  Otherwise
+ * INET_ERR_INVALID_ARG.  interactions_out (may be NULL) gets the net's
+ * interaction count. */
+inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out, uint64_t* interactions_out);
+
+/* Per-net counters; live and residual agents come from the readback
+ * snapshot. */
+inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out);
+
+/* Copies the per-step trace of the last inet_reduce() with opts->trace set:
+ * frontier size and live agents after each step.  *n_out gets the number of
+ * steps recorded (at most cap are copied; either array may be NULL). */
+inet_status inet_trace(inet_ctx* ctx, int64_t* frontier, int64_t* live, size_t cap, size_t* n_out);
+
+/* Drops every net and empties the arena (capacities and rules are kept).
+ * Clears a poisoned state. */
+inet_status inet_reset(inet_ctx* ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+const char* inet_last_error(const inet_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INET_H */

@@ -1,0 +1,120 @@
+"""GB300 evaluator for interaction nets (the data-parallel reduction loop of
+the lightweight interaction calculus, Sec. 3 of Jiresch, "Towards a
+GPU-based implementation of interaction nets").
+
+`capi` mirrors the C ABI one function per entry point; `Evaluator` wraps a
+context whose device workspace and stream come from PyTorch.
+"""
+from __future__ import annotations
+
+import importlib
+
+# The CUDA library is loaded on first use of `capi` (or anything that needs
+# it), so `paper_1404_0076_gb300.build` can be imported before it exists;
+# using the evaluator without the library raises ImportError.
+MODES = {"plain": 0, "graph": 1, "persistent": 2}
+
+
+def __getattr__(name):
+    if name == "capi":
+        return importlib.import_module(".capi", __name__)
+    if name == "InetError":
+        return importlib.import_module(".capi", __name__).InetError
+    raise AttributeError(name)
+
+
+class _Lazy:
+    def __getattr__(self, name):
+        return getattr(importlib.import_module(".capi", __name__), name)
+
+
+capi_lazy = _Lazy()
+
+
+class Evaluator:
+    """One evaluation context on one GPU (device < 0: host-only, for parsing
+    and loading without a GPU).
+
+    The workspace is one uint8 tensor from PyTorch's caching allocator and
+    the context runs on PyTorch's current stream of that device."""
+
+    def __init__(self, device: int = 0, max_agents: int = 0, max_vars: int = 0, max_pairs: int = 0,
+                 max_nets: int = 0, use_torch: bool = True):
+        from . import capi
+        self.cfg = capi.inet_arena_cfg(max_agents, max_vars, max_pairs, max_nets, 0)
+        self.device = device
+        self._ws = None
+        stream = None
+        if device >= 0 and use_torch:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.ctx = capi.inet_create(device, stream, self.cfg)
+        if device >= 0 and use_torch:
+            import torch
+            nbytes = capi.inet_workspace_bytes(self.cfg)
+            ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+            off = (-ws.data_ptr()) % 256
+            self._ws = ws
+            capi.inet_attach_workspace(self.ctx, ws.data_ptr() + off, nbytes)
+
+    # -- lifecycle
+    def close(self):
+        from . import capi
+        if getattr(self, "ctx", None):
+            capi.inet_destroy(self.ctx)
+            self.ctx = None
+        self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API
+    def load_rules(self, text: str) -> None:
+        capi_lazy.inet_load_rules(self.ctx, text)
+
+    def rules(self) -> list[dict]:
+        return [capi_lazy.inet_rule_info(self.ctx, i) for i in range(capi_lazy.inet_rule_count(self.ctx))]
+
+    def load_net(self, text: str) -> int:
+        return capi_lazy.inet_load_net(self.ctx, text)
+
+    def load_nets(self, texts) -> list[int]:
+        return [capi_lazy.inet_load_net(self.ctx, t) for t in texts]
+
+    def reduce(self, net_ids, mode: str = "persistent", block: int = 0, grid: int = 0, solo_max: int = 0,
+               max_steps: int = 0, timeout_s: float = 0.0, trace: bool = False, check: bool = True) -> dict:
+        o = capi_lazy.inet_reduce_opts(MODES[mode], block, grid, solo_max, max_steps, int(timeout_s * 1e9),
+                                  1 if trace else 0, 0)
+        rc, st = capi_lazy.inet_reduce(self.ctx, list(net_ids), o, check=check)
+        return {"status": capi_lazy.STATUS_NAMES.get(rc, rc), "interactions": st.interactions, "steps": st.steps,
+                "max_frontier": st.max_frontier, "live_agents": st.live_agents,
+                "peak_live_agents": st.peak_live_agents, "pending_pairs": st.pending_pairs,
+                "device_ms": st.device_ms, "launches": st.launches,
+                "per_rule": list(st.per_rule[:st.n_rules])}
+
+    def readback(self, net_id: int) -> str:
+        return capi_lazy.inet_readback(self.ctx, net_id)
+
+    def readback_nat(self, net_id: int) -> tuple[int, int]:
+        return capi_lazy.inet_readback_nat(self.ctx, net_id)
+
+    def net_info(self, net_id: int) -> dict:
+        return capi_lazy.inet_net_info(self.ctx, net_id)
+
+    def trace(self):
+        return capi_lazy.inet_trace(self.ctx)
+
+    def reset(self) -> None:
+        capi_lazy.inet_reset(self.ctx)
+
+
+__all__ = ["Evaluator", "InetError", "capi", "MODES"]

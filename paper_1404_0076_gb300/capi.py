@@ -1,0 +1,225 @@
+"""ctypes binding of the evaluator's C ABI (include/inet.h).
+
+Every C entry point has a Python function of the same name here; they only
+marshal arguments and turn a negative status into InetError.  All of the
+reduction runs in the CUDA library; if the library is missing this module
+raises at import time instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libinet.so")
+
+INET_OK = 0
+INET_ERR_INVALID_ARG = -1
+INET_ERR_PARSE = -2
+INET_ERR_LINEARITY = -3
+INET_ERR_NO_RULE = -4
+INET_ERR_ARENA_FULL = -5
+INET_ERR_STEP_LIMIT = -6
+INET_ERR_TIMEOUT = -7
+INET_ERR_CUDA = -8
+INET_ERR_NO_DEVICE = -9
+INET_ERR_STATE = -10
+
+STATUS_NAMES = {
+    0: "OK", -1: "INVALID_ARG", -2: "PARSE", -3: "LINEARITY", -4: "NO_RULE", -5: "ARENA_FULL",
+    -6: "STEP_LIMIT", -7: "TIMEOUT", -8: "CUDA", -9: "NO_DEVICE", -10: "STATE",
+}
+
+INET_MODE_PLAIN = 0
+INET_MODE_GRAPH = 1
+INET_MODE_PERSISTENT = 2
+INET_MAX_RULES = 64
+
+EXPORTED = [
+    "inet_workspace_bytes", "inet_create", "inet_attach_workspace", "inet_destroy",
+    "inet_load_rules", "inet_rule_count", "inet_rule_info", "inet_load_net", "inet_reduce",
+    "inet_readback", "inet_readback_nat", "inet_net_info", "inet_trace", "inet_reset",
+    "inet_last_error",
+]
+
+
+class inet_arena_cfg(C.Structure):
+    _fields_ = [("max_agents", C.c_uint64), ("max_vars", C.c_uint64), ("max_pairs", C.c_uint64),
+                ("max_nets", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class inet_reduce_opts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("block", C.c_int32), ("grid", C.c_int32), ("solo_max", C.c_int32),
+                ("max_steps", C.c_uint64), ("timeout_ns", C.c_uint64), ("trace", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class inet_reduce_stats(C.Structure):
+    _fields_ = [("interactions", C.c_uint64), ("steps", C.c_uint64), ("max_frontier", C.c_uint64),
+                ("live_agents", C.c_int64), ("peak_live_agents", C.c_int64), ("pending_pairs", C.c_uint64),
+                ("device_ms", C.c_double), ("n_rules", C.c_uint32), ("launches", C.c_uint32),
+                ("per_rule", C.c_uint64 * INET_MAX_RULES)]
+
+
+class inet_net_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("reduced", C.c_int32), ("interactions", C.c_uint64),
+                ("pending_pairs", C.c_uint64), ("live_agents", C.c_int64), ("residual_agents", C.c_int64)]
+
+
+class inet_rule_desc(C.Structure):
+    _fields_ = [("name", C.c_char * 64), ("arity_alpha", C.c_int32), ("arity_beta", C.c_int32),
+                ("n_new", C.c_int32), ("new_ports", C.c_int32), ("n_fresh", C.c_int32), ("n_link", C.c_int32)]
+
+
+class InetError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "or python -m paper_1404_0076_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "inet_workspace_bytes": ([C.POINTER(inet_arena_cfg), C.POINTER(C.c_size_t)], C.c_int32),
+        "inet_create": ([C.POINTER(P), C.c_int, P, C.POINTER(inet_arena_cfg)], C.c_int32),
+        "inet_attach_workspace": ([P, P, C.c_size_t], C.c_int32),
+        "inet_destroy": ([P], None),
+        "inet_load_rules": ([P, C.c_char_p, C.c_size_t], C.c_int32),
+        "inet_rule_count": ([P, C.POINTER(C.c_int32)], C.c_int32),
+        "inet_rule_info": ([P, C.c_int32, C.POINTER(inet_rule_desc)], C.c_int32),
+        "inet_load_net": ([P, C.c_char_p, C.c_size_t, C.POINTER(C.c_int32)], C.c_int32),
+        "inet_reduce": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(inet_reduce_opts),
+                         C.POINTER(inet_reduce_stats)], C.c_int32),
+        "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
+        "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
+        "inet_net_info": ([P, C.c_int32, C.POINTER(inet_net_stats)], C.c_int32),
+        "inet_trace": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_size_t, C.POINTER(C.c_size_t)],
+                       C.c_int32),
+        "inet_reset": ([P], C.c_int32),
+        "inet_last_error": ([P], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _check(ctx, status: int) -> int:
+    if status != INET_OK:
+        msg = LIB.inet_last_error(ctx).decode(errors="replace") if ctx else ""
+        raise InetError(status, msg)
+    return status
+
+
+# --- one Python function per C entry point ------------------------------------
+
+def inet_workspace_bytes(cfg: inet_arena_cfg | None = None) -> int:
+    n = C.c_size_t()
+    _check(None, LIB.inet_workspace_bytes(C.byref(cfg) if cfg else None, C.byref(n)))
+    return n.value
+
+
+def inet_create(device: int, stream: int | None = None, cfg: inet_arena_cfg | None = None) -> C.c_void_p:
+    ctx = C.c_void_p()
+    st = LIB.inet_create(C.byref(ctx), device, C.c_void_p(stream) if stream else None,
+                         C.byref(cfg) if cfg else None)
+    if st != INET_OK:
+        raise InetError(st, "inet_create failed")
+    return ctx
+
+
+def inet_attach_workspace(ctx, dptr: int, nbytes: int) -> None:
+    _check(ctx, LIB.inet_attach_workspace(ctx, C.c_void_p(dptr), nbytes))
+
+
+def inet_destroy(ctx) -> None:
+    LIB.inet_destroy(ctx)
+
+
+def inet_load_rules(ctx, text: str) -> None:
+    b = text.encode()
+    _check(ctx, LIB.inet_load_rules(ctx, b, len(b)))
+
+
+def inet_rule_count(ctx) -> int:
+    n = C.c_int32()
+    _check(ctx, LIB.inet_rule_count(ctx, C.byref(n)))
+    return n.value
+
+
+def inet_rule_info(ctx, rule: int) -> dict:
+    d = inet_rule_desc()
+    _check(ctx, LIB.inet_rule_info(ctx, rule, C.byref(d)))
+    return {"name": d.name.decode(), "arity_alpha": d.arity_alpha, "arity_beta": d.arity_beta,
+            "n_new": d.n_new, "new_ports": d.new_ports, "n_fresh": d.n_fresh, "n_link": d.n_link}
+
+
+def inet_load_net(ctx, text: str) -> int:
+    b = text.encode()
+    nid = C.c_int32()
+    _check(ctx, LIB.inet_load_net(ctx, b, len(b), C.byref(nid)))
+    return nid.value
+
+
+def inet_reduce(ctx, net_ids, opts: inet_reduce_opts | None = None, check: bool = True):
+    """Returns (status, inet_reduce_stats).  With check=True a non-OK status
+    raises InetError (carrying the stats as .stats)."""
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    st = inet_reduce_stats()
+    rc = LIB.inet_reduce(ctx, ids, len(net_ids), C.byref(opts) if opts else None, C.byref(st))
+    if check and rc != INET_OK:
+        err = InetError(rc, LIB.inet_last_error(ctx).decode(errors="replace"))
+        err.stats = st
+        raise err
+    return rc, st
+
+
+def inet_readback(ctx, net_id: int) -> str:
+    need = C.c_size_t()
+    rc = LIB.inet_readback(ctx, net_id, None, 0, C.byref(need))
+    if rc not in (INET_OK, INET_ERR_INVALID_ARG) or need.value == 0:
+        _check(ctx, rc)
+    buf = C.create_string_buffer(need.value)
+    _check(ctx, LIB.inet_readback(ctx, net_id, buf, need.value, C.byref(need)))
+    return buf.value.decode()
+
+
+def inet_readback_nat(ctx, net_id: int) -> tuple[int, int]:
+    v = C.c_uint64()
+    n = C.c_uint64()
+    _check(ctx, LIB.inet_readback_nat(ctx, net_id, C.byref(v), C.byref(n)))
+    return v.value, n.value
+
+
+def inet_net_info(ctx, net_id: int) -> dict:
+    s = inet_net_stats()
+    _check(ctx, LIB.inet_net_info(ctx, net_id, C.byref(s)))
+    return {"status": STATUS_NAMES.get(s.status, s.status), "reduced": bool(s.reduced),
+            "interactions": s.interactions, "pending_pairs": s.pending_pairs,
+            "live_agents": s.live_agents, "residual_agents": s.residual_agents}
+
+
+def inet_trace(ctx) -> tuple[list[int], list[int]]:
+    n = C.c_size_t()
+    _check(ctx, LIB.inet_trace(ctx, None, None, 0, C.byref(n)))
+    fr = (C.c_int64 * max(1, n.value))()
+    lv = (C.c_int64 * max(1, n.value))()
+    _check(ctx, LIB.inet_trace(ctx, fr, lv, n.value, C.byref(n)))
+    return list(fr[:n.value]), list(lv[:n.value])
+
+
+def inet_reset(ctx) -> None:
+    _check(ctx, LIB.inet_reset(ctx))
+
+
+def inet_last_error(ctx) -> str:
+    return LIB.inet_last_error(ctx).decode(errors="replace")

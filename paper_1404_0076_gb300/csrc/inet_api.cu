@@ -1,0 +1,816 @@
+// C ABI of the evaluator (include/inet.h): context, device workspace, net
+// loading, the three drivers of the step loop (plain host loop, CUDA graph
+// with a conditional WHILE node, persistent cooperative kernel) and readback.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "inet.h"
+#include "inet_kernels.cuh"
+#include "inet_text.h"
+
+using namespace inet;
+
+namespace {
+
+constexpr uint32_t kTraceCap = 1u << 20;
+constexpr uint64_t kDefaultAgents = 1ull << 22;
+constexpr uint64_t kDefaultVars = 1ull << 22;
+constexpr uint64_t kDefaultPairs = 1ull << 21;
+constexpr uint32_t kDefaultNets = 1u << 16;
+constexpr unsigned long long kDefaultTimeoutNs = 10ull * 1000 * 1000 * 1000;
+constexpr unsigned long long kSliceNs = 2ull * 1000 * 1000 * 1000;
+
+struct Layout {
+  size_t ctrl, node, var, front0, front1, afree, vfree, netctr, netstat, hist, table, tmpl, arity,
+      trace_front, trace_live, total;
+};
+
+inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
+  inet_arena_cfg c;
+  memset(&c, 0, sizeof c);
+  if (in) c = *in;
+  if (!c.max_agents) c.max_agents = kDefaultAgents;
+  if (!c.max_vars) c.max_vars = kDefaultVars;
+  if (!c.max_pairs) c.max_pairs = kDefaultPairs;
+  if (!c.max_nets) c.max_nets = kDefaultNets;
+  return c;
+}
+
+bool valid_cfg(const inet_arena_cfg& c) {
+  return c.max_agents <= kMaxIndex + 1ull && c.max_vars <= kMaxIndex + 1ull && c.max_pairs <= 0xFFFFFFFFull &&
+         c.max_nets <= kMaxNetSlots;
+}
+
+Layout layout_of(const inet_arena_cfg& c) {
+  Layout L;
+  size_t b = 0;
+  auto take = [&](size_t n) { b = (b + 255) / 256 * 256; size_t at = b; b += n; return at; };
+  L.ctrl = take(sizeof(Ctrl));
+  L.node = take(sizeof(Node) * c.max_agents);
+  L.var = take(sizeof(uint32_t) * c.max_vars);
+  L.front0 = take(sizeof(Pair) * c.max_pairs);
+  L.front1 = take(sizeof(Pair) * c.max_pairs);
+  L.afree = take(sizeof(uint32_t) * c.max_agents);
+  L.vfree = take(sizeof(uint32_t) * c.max_vars);
+  L.netctr = take(sizeof(unsigned long long) * c.max_nets);
+  L.netstat = take(sizeof(int32_t) * c.max_nets);
+  L.hist = take(sizeof(unsigned long long) * INET_MAX_RULES);
+  L.table = take(sizeof(int16_t) * kMaxLabels * kMaxLabels);
+  L.tmpl = take(sizeof(Template) * INET_MAX_RULES);
+  L.arity = take(kMaxLabels);
+  L.trace_front = take(sizeof(long long) * kTraceCap);
+  L.trace_live = take(sizeof(long long) * kTraceCap);
+  L.total = take(0) + 256;
+  return L;
+}
+
+struct NetRec {
+  bool used = false;
+  bool started = false;           // its pairs were handed to the device
+  std::vector<uint32_t> iface;
+  std::vector<Pair> pairs;        // initial active pairs, until started
+};
+
+}  // namespace
+
+struct inet_ctx {
+  int device = -1;
+  bool host_only = true;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  inet_arena_cfg cfg{};
+  Layout lay{};
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  bool ws_ready = false;
+  Dev dev{};
+  int num_sms = 0;
+  // rules
+  bool have_rules = false;
+  CompiledRules rules;
+  // host mirrors of device counters
+  uint64_t a_bump = 0, v_bump = 0;
+  int64_t live = 0;
+  uint32_t step = 0;
+  uint32_t fcount[2] = {0, 0};
+  // nets
+  std::vector<NetRec> nets;
+  // staged loads
+  std::vector<Node> st_nodes;
+  uint64_t st_a0 = 0;
+  std::vector<uint32_t> st_vars;
+  uint64_t st_v0 = 0;
+  std::vector<unsigned long long> st_netctr;
+  uint32_t st_net0 = 0;
+  // device-side per-net copies (after the last reduce)
+  std::vector<unsigned long long> h_netctr;
+  std::vector<int32_t> h_netstat;
+  // readback snapshot
+  bool snap_valid = false;
+  std::vector<Node> snap_nodes;
+  std::vector<uint32_t> snap_vars;
+  std::vector<int64_t> snap_live;
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int g_block = 0, g_grid = 0;
+  // trace of the last reduce
+  std::vector<long long> tr_front, tr_live;
+  bool poisoned = false;
+  std::string err;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1, want = -1;
+  explicit DeviceGuard(int d) : want(d) {
+    if (d < 0) return;
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (want >= 0 && prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+};
+
+inet_status fail(inet_ctx* c, inet_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ctx->poisoned = true;                                                               \
+      return fail(ctx, INET_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                     \
+  } while (0)
+
+template <class T>
+T* at(inet_ctx* ctx, size_t off) {
+  return reinterpret_cast<T*>(ctx->ws + off);
+}
+
+void fill_dev(inet_ctx* ctx) {
+  Dev& d = ctx->dev;
+  const Layout& L = ctx->lay;
+  d.node = at<Node>(ctx, L.node);
+  d.var = at<uint32_t>(ctx, L.var);
+  d.front[0] = at<Pair>(ctx, L.front0);
+  d.front[1] = at<Pair>(ctx, L.front1);
+  d.afree = at<uint32_t>(ctx, L.afree);
+  d.vfree = at<uint32_t>(ctx, L.vfree);
+  d.netctr = at<unsigned long long>(ctx, L.netctr);
+  d.netstat = at<int32_t>(ctx, L.netstat);
+  d.rule_hist = at<unsigned long long>(ctx, L.hist);
+  d.ctrl = at<Ctrl>(ctx, L.ctrl);
+  d.table = at<int16_t>(ctx, L.table);
+  d.tmpl = at<Template>(ctx, L.tmpl);
+  d.arity = at<uint8_t>(ctx, L.arity);
+  d.trace_front = at<long long>(ctx, L.trace_front);
+  d.trace_live = at<long long>(ctx, L.trace_live);
+  d.cap_agents = ctx->cfg.max_agents;
+  d.cap_vars = ctx->cfg.max_vars;
+  d.cap_pairs = (uint32_t)ctx->cfg.max_pairs;
+  d.trace_cap = kTraceCap;
+  d.max_nets = ctx->cfg.max_nets;
+  d.n_labels = (uint32_t)ctx->rules.n_labels();
+  d.n_tmpl = (uint32_t)ctx->rules.tmpl.size();
+  d.timeout_ns = kDefaultTimeoutNs;
+  d.slice_ns = kSliceNs;
+  d.solo_max = 0;
+  d.use_cond = 0;
+  d.cond = 0;
+}
+
+inet_status upload_rules(inet_ctx* ctx) {
+  if (!ctx->ws_ready || !ctx->have_rules) return INET_OK;
+  const CompiledRules& r = ctx->rules;
+  std::vector<uint8_t> ar(kMaxLabels, 0);
+  for (size_t i = 0; i < r.arity.size(); i++) ar[i] = (uint8_t)r.arity[i];
+  if (!r.table.empty())
+    CK(cudaMemcpyAsync(ctx->ws + ctx->lay.table, r.table.data(), r.table.size() * sizeof(int16_t),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  if (!r.tmpl.empty())
+    CK(cudaMemcpyAsync(ctx->ws + ctx->lay.tmpl, r.tmpl.data(), r.tmpl.size() * sizeof(Template),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->ws + ctx->lay.arity, ar.data(), kMaxLabels, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  fill_dev(ctx);
+  return INET_OK;
+}
+
+// Zeroes the control block and the per-net and name-slot arrays.
+inet_status clear_device(inet_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.ctrl, 0, sizeof(Ctrl), ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.var, 0, sizeof(uint32_t) * ctx->cfg.max_vars, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.netctr, 0, sizeof(unsigned long long) * ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.netstat, 0, sizeof(int32_t) * ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
+  uint32_t never = 0xFFFFFFFFu;
+  CK(cudaMemcpyAsync(&ctx->dev.ctrl->stop_step, &never, 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return INET_OK;
+}
+
+inet_status ensure_workspace(inet_ctx* ctx) {
+  if (ctx->ws_ready) return INET_OK;
+  if (!ctx->ws) {
+    void* p = nullptr;
+    CK(cudaMalloc(&p, ctx->lay.total));
+    ctx->ws = static_cast<unsigned char*>(p);
+    ctx->ws_bytes = ctx->lay.total;
+    ctx->own_ws = true;
+  }
+  ctx->ws_ready = true;
+  fill_dev(ctx);
+  inet_status s = clear_device(ctx);
+  if (s) return s;
+  return upload_rules(ctx);
+}
+
+// Copies staged nets to the device and the host-side counters to the control block.
+inet_status upload_staged(inet_ctx* ctx) {
+  if (!ctx->st_nodes.empty())
+    CK(cudaMemcpyAsync(ctx->dev.node + ctx->st_a0, ctx->st_nodes.data(), ctx->st_nodes.size() * sizeof(Node),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  if (!ctx->st_vars.empty())
+    CK(cudaMemcpyAsync(ctx->dev.var + ctx->st_v0, ctx->st_vars.data(), ctx->st_vars.size() * sizeof(uint32_t),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  if (!ctx->st_netctr.empty()) {
+    CK(cudaMemcpyAsync(ctx->dev.netctr + ctx->st_net0, ctx->st_netctr.data(),
+                       ctx->st_netctr.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->dev.netstat + ctx->st_net0, 0, ctx->st_netctr.size() * sizeof(int32_t), ctx->stream));
+  }
+  const bool any = !ctx->st_nodes.empty() || !ctx->st_vars.empty() || !ctx->st_netctr.empty();
+  if (any) {
+    static thread_local unsigned long long hb[2];
+    static thread_local long long hl;
+    hb[0] = ctx->a_bump;
+    hb[1] = ctx->v_bump;
+    hl = ctx->live;
+    CK(cudaMemcpyAsync(&ctx->dev.ctrl->a_bump, &hb[0], 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->dev.ctrl->v_bump, &hb[1], 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->dev.ctrl->live, &hl, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->st_nodes.clear();
+  ctx->st_vars.clear();
+  ctx->st_netctr.clear();
+  ctx->st_a0 = ctx->a_bump;
+  ctx->st_v0 = ctx->v_bump;
+  ctx->st_net0 = (uint32_t)ctx->nets.size();
+  ctx->snap_valid = false;
+  return INET_OK;
+}
+
+inet_status build_graph(inet_ctx* ctx, int block, int grid, size_t smem) {
+  if (ctx->gexec && ctx->g_block == block && ctx->g_grid == grid) return INET_OK;
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  CK(cudaGraphCreate(&ctx->graph, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, ctx->graph, 1, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  memset(cp_raw, 0, sizeof cp_raw);
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  CK(cudaGraphAddNode(&cn, ctx->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  Dev d = ctx->dev;
+  d.cond = h;
+  d.use_cond = 1;
+  void* args[] = {&d};
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof kp);
+  kp.func = (void*)k_step;
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  cudaGraphNode_t kn;
+  CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
+  CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+  ctx->g_block = block;
+  ctx->g_grid = grid;
+  return INET_OK;
+}
+
+void drop_graph(inet_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
+  ctx->g_block = ctx->g_grid = 0;
+}
+
+inet_status ensure_snapshot(inet_ctx* ctx) {
+  if (ctx->snap_valid) return INET_OK;
+  ctx->snap_nodes.resize(ctx->a_bump);
+  ctx->snap_vars.resize(ctx->v_bump);
+  if (ctx->a_bump)
+    CK(cudaMemcpyAsync(ctx->snap_nodes.data(), ctx->dev.node, ctx->a_bump * sizeof(Node), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (ctx->v_bump)
+    CK(cudaMemcpyAsync(ctx->snap_vars.data(), ctx->dev.var, ctx->v_bump * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  Ctrl hc;
+  CK(cudaMemcpyAsync(&hc, ctx->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // free agent slots: ring entries [a_head, a_tail)
+  std::vector<uint8_t> is_free(ctx->a_bump, 0);
+  const uint64_t cap = ctx->cfg.max_agents;
+  uint64_t nfree = hc.a_tail - hc.a_head;
+  if (nfree) {
+    std::vector<uint32_t> ring(nfree);
+    uint64_t h = hc.a_head % cap;
+    uint64_t first = std::min<uint64_t>(nfree, cap - h);
+    CK(cudaMemcpyAsync(ring.data(), ctx->dev.afree + h, first * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (nfree > first)
+      CK(cudaMemcpyAsync(ring.data() + first, ctx->dev.afree, (nfree - first) * 4, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (uint32_t s : ring)
+      if (s < ctx->a_bump) is_free[s] = 1;
+  }
+  ctx->snap_live.assign(ctx->nets.size(), 0);
+  for (uint64_t i = 0; i < ctx->a_bump; i++) {
+    if (is_free[i]) continue;
+    uint32_t net = (uint32_t)ctx->snap_nodes[i].head >> 8;
+    if (net < ctx->snap_live.size()) ctx->snap_live[net]++;
+  }
+  ctx->snap_valid = true;
+  return INET_OK;
+}
+
+inet_status check_net(inet_ctx* ctx, int32_t id) {
+  if (id < 0 || (size_t)id >= ctx->nets.size() || !ctx->nets[(size_t)id].used)
+    return fail(ctx, INET_ERR_INVALID_ARG, "unknown net id " + std::to_string(id));
+  return INET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+inet_status inet_workspace_bytes(const inet_arena_cfg* cfg, size_t* bytes_out) {
+  if (!bytes_out) return INET_ERR_INVALID_ARG;
+  inet_arena_cfg c = with_defaults(cfg);
+  if (!valid_cfg(c)) return INET_ERR_INVALID_ARG;
+  *bytes_out = layout_of(c).total;
+  return INET_OK;
+}
+
+inet_status inet_create(inet_ctx** out, int device, void* stream, const inet_arena_cfg* cfg) {
+  if (!out) return INET_ERR_INVALID_ARG;
+  *out = nullptr;
+  inet_arena_cfg c = with_defaults(cfg);
+  if (!valid_cfg(c)) return INET_ERR_INVALID_ARG;
+  inet_ctx* ctx = new inet_ctx();
+  ctx->cfg = c;
+  ctx->lay = layout_of(c);
+  ctx->device = device;
+  ctx->host_only = device < 0;
+  if (!ctx->host_only) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
+      delete ctx;
+      return INET_ERR_NO_DEVICE;
+    }
+    DeviceGuard g(device);
+    if (stream) {
+      ctx->stream = static_cast<cudaStream_t>(stream);
+    } else if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) == cudaSuccess) {
+      ctx->own_stream = true;
+    } else {
+      delete ctx;
+      return INET_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+      delete ctx;
+      return INET_ERR_CUDA;
+    }
+  }
+  *out = ctx;
+  return INET_OK;
+}
+
+inet_status inet_attach_workspace(inet_ctx* ctx, void* dptr, size_t bytes) {
+  if (!ctx || !dptr) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (ctx->ws) return fail(ctx, INET_ERR_STATE, "workspace already set");
+  if (bytes < ctx->lay.total || (reinterpret_cast<uintptr_t>(dptr) & 255))
+    return fail(ctx, INET_ERR_INVALID_ARG, "workspace too small or not 256-byte aligned");
+  DeviceGuard g(ctx->device);
+  ctx->ws = static_cast<unsigned char*>(dptr);
+  ctx->ws_bytes = bytes;
+  ctx->own_ws = false;
+  return ensure_workspace(ctx);
+}
+
+void inet_destroy(inet_ctx* ctx) {
+  if (!ctx) return;
+  if (!ctx->host_only) {
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  }
+  delete ctx;
+}
+
+inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len) {
+  if (!ctx || (!text && len)) return INET_ERR_INVALID_ARG;
+  for (auto& n : ctx->nets)
+    if (n.used) return fail(ctx, INET_ERR_STATE, "rules cannot change while nets are loaded (inet_reset first)");
+  CompiledRules r;
+  std::string err;
+  int rc = compile_rules(std::string(text ? text : "", len), r, err);
+  if (rc) return fail(ctx, rc, err);
+  ctx->rules = std::move(r);
+  ctx->have_rules = true;
+  if (ctx->host_only) return INET_OK;
+  DeviceGuard g(ctx->device);
+  drop_graph(ctx);
+  return upload_rules(ctx);
+}
+
+inet_status inet_rule_count(const inet_ctx* ctx, int32_t* n_out) {
+  if (!ctx || !n_out) return INET_ERR_INVALID_ARG;
+  *n_out = (int32_t)ctx->rules.tmpl.size();
+  return INET_OK;
+}
+
+inet_status inet_rule_info(const inet_ctx* ctx, int32_t rule, inet_rule_desc* out) {
+  if (!ctx || !out || rule < 0 || (size_t)rule >= ctx->rules.tmpl.size()) return INET_ERR_INVALID_ARG;
+  const CompiledRules& r = ctx->rules;
+  const Template& t = r.tmpl[(size_t)rule];
+  memset(out, 0, sizeof *out);
+  snprintf(out->name, sizeof out->name, "%s", r.rule_names[(size_t)rule].c_str());
+  // the LHS symbols are the two labels whose table entry points at this rule
+  int L = r.n_labels();
+  for (int i = 0; i < L; i++)
+    for (int j = 0; j < L; j++)
+      if (r.table[(size_t)i * L + j] == (int16_t)(rule << 1)) {
+        out->arity_alpha = r.arity[(size_t)i];
+        out->arity_beta = r.arity[(size_t)j];
+      }
+  out->n_new = t.n_new;
+  for (int j = 0; j < t.n_new; j++) out->new_ports += r.arity[t.lab[j]];
+  out->n_fresh = t.n_fresh;
+  out->n_link = t.n_link;
+  return INET_OK;
+}
+
+inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* net_id_out) {
+  if (!ctx || (!text && len) || !net_id_out) return INET_ERR_INVALID_ARG;
+  if (!ctx->have_rules) return fail(ctx, INET_ERR_STATE, "load rules first");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  if (ctx->nets.size() >= ctx->cfg.max_nets) return fail(ctx, INET_ERR_ARENA_FULL, "no free net slot");
+  if (!ctx->host_only) {
+    DeviceGuard g(ctx->device);
+    inet_status s = ensure_workspace(ctx);
+    if (s) return s;
+  }
+  const uint32_t slot = (uint32_t)ctx->nets.size();
+  FlatNet fn;
+  std::string err;
+  int rc = flatten_net(std::string(text ? text : "", len), ctx->rules, slot, (uint32_t)ctx->a_bump,
+                       (uint32_t)ctx->v_bump, fn, err);
+  if (rc) return fail(ctx, rc, err);
+  if (ctx->a_bump + fn.nodes.size() > ctx->cfg.max_agents || ctx->v_bump + fn.vars.size() > ctx->cfg.max_vars)
+    return fail(ctx, INET_ERR_ARENA_FULL, "net does not fit the arena");
+  if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
+    ctx->st_a0 = ctx->a_bump;
+    ctx->st_v0 = ctx->v_bump;
+    ctx->st_net0 = slot;
+  }
+  ctx->st_nodes.insert(ctx->st_nodes.end(), fn.nodes.begin(), fn.nodes.end());
+  ctx->st_vars.insert(ctx->st_vars.end(), fn.vars.begin(), fn.vars.end());
+  ctx->st_netctr.push_back((unsigned long long)fn.pairs.size() << kNetPairShift);
+  ctx->a_bump += fn.nodes.size();
+  ctx->v_bump += fn.vars.size();
+  ctx->live += (int64_t)fn.nodes.size();
+  NetRec nr;
+  nr.used = true;
+  nr.iface = std::move(fn.iface);
+  nr.pairs = std::move(fn.pairs);
+  ctx->nets.push_back(std::move(nr));
+  ctx->h_netctr.push_back((unsigned long long)ctx->nets.back().pairs.size() << kNetPairShift);
+  ctx->h_netstat.push_back(0);
+  ctx->snap_valid = false;
+  *net_id_out = (int32_t)slot;
+  return INET_OK;
+}
+
+inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const inet_reduce_opts* opts,
+                        inet_reduce_stats* stats) {
+  if (!ctx || n < 0 || (n > 0 && !net_ids)) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context cannot reduce");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  if (!ctx->have_rules) return fail(ctx, INET_ERR_STATE, "load rules first");
+  inet_reduce_opts o;
+  memset(&o, 0, sizeof o);
+  if (opts) o = *opts;
+  const int B = o.block ? o.block : 256;
+  if (B < 64 || B > 512 || B % 32) return fail(ctx, INET_ERR_INVALID_ARG, "block must be a multiple of 32 in [64, 512]");
+  if (o.mode < INET_MODE_PLAIN || o.mode > INET_MODE_PERSISTENT) return fail(ctx, INET_ERR_INVALID_ARG, "bad mode");
+  for (int32_t i = 0; i < n; i++) {
+    inet_status s = check_net(ctx, net_ids[i]);
+    if (s) return s;
+    if (ctx->nets[(size_t)net_ids[i]].started) return fail(ctx, INET_ERR_INVALID_ARG, "net already reduced");
+  }
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  s = upload_staged(ctx);
+  if (s) return s;
+  // new active pairs join the current frontier
+  std::vector<Pair> add;
+  for (int32_t i = 0; i < n; i++) {
+    NetRec& nr = ctx->nets[(size_t)net_ids[i]];
+    add.insert(add.end(), nr.pairs.begin(), nr.pairs.end());
+    nr.pairs.clear();
+    nr.pairs.shrink_to_fit();
+    nr.started = true;
+  }
+  const uint32_t cur = ctx->step & 1u;
+  if ((uint64_t)ctx->fcount[cur] + add.size() > ctx->cfg.max_pairs)
+    return fail(ctx, INET_ERR_ARENA_FULL, "frontier capacity exceeded");
+  if (!add.empty())
+    CK(cudaMemcpyAsync(ctx->dev.front[cur] + ctx->fcount[cur], add.data(), add.size() * sizeof(Pair),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  // per-call control fields
+  struct {
+    uint32_t step, done;
+    int32_t error;
+    uint32_t error_info, stop_step, hit_limit, trace_on, call_step0;
+    int32_t fatal;
+    uint32_t hit_slice;
+    unsigned long long max_frontier;
+    long long peak_live;
+    unsigned long long slice_t0;
+  } head;
+  static_assert(sizeof(head) == offsetof(Ctrl, pad0), "control head layout");
+  memset(&head, 0, sizeof head);
+  head.step = ctx->step;
+  head.stop_step = o.max_steps ? (uint32_t)std::min<uint64_t>(0xFFFFFFFEull, ctx->step + o.max_steps) : 0xFFFFFFFFu;
+  head.trace_on = o.trace ? 1u : 0u;
+  head.call_step0 = ctx->step;
+  head.peak_live = ctx->live;
+  uint32_t fc[2] = {ctx->fcount[0], ctx->fcount[1]};
+  fc[cur] += (uint32_t)add.size();
+  CK(cudaMemcpyAsync(ctx->dev.ctrl, &head, sizeof head, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dev.ctrl->fcount, fc, sizeof fc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->dev.rule_hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
+  Dev d = ctx->dev;
+  d.timeout_ns = o.timeout_ns ? o.timeout_ns : kDefaultTimeoutNs;
+  const size_t smem = smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl);
+  CK(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(cudaEventRecord(ctx->ev0, ctx->stream));
+  uint64_t launches = 0;
+  if (fc[cur] > 0) {
+    if (o.mode == INET_MODE_PLAIN) {
+      // one launch and one 16-byte read of the frontier size per step
+      uint32_t pending = fc[cur];
+      for (;;) {
+        const uint32_t grid = std::max<uint32_t>(1, (pending + (uint32_t)B - 1) / (uint32_t)B);
+        k_step<<<grid, B, smem, ctx->stream>>>(d);
+        CK(cudaGetLastError());
+        launches++;
+        uint32_t st[4];  // step, done, error, error_info
+        uint32_t fcn[2];
+        CK(cudaMemcpyAsync(st, ctx->dev.ctrl, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(fcn, ctx->dev.ctrl->fcount, sizeof fcn, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (st[1]) break;
+        pending = fcn[st[0] & 1u];
+        if (pending == 0) break;
+      }
+    } else {
+      // GRAPH and PERSISTENT run many steps per launch; a launch also ends
+      // when its time slice is over (hit_slice), and is then relaunched.
+      int grid = o.grid;
+      if (o.mode == INET_MODE_GRAPH) {
+        if (grid <= 0) {
+          int per = 0;
+          CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step, B, smem));
+          grid = std::max(1, per) * ctx->num_sms;
+        }
+        s = build_graph(ctx, B, grid, smem);
+        if (s) return s;
+      } else {
+        int per = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem));
+        const int maxg = std::max(1, per) * ctx->num_sms;
+        grid = grid > 0 ? std::min(grid, maxg) : maxg;
+        d.solo_max = o.solo_max < 0 ? 0u : (o.solo_max == 0 ? (uint32_t)B : (uint32_t)o.solo_max);
+      }
+      for (;;) {
+        if (o.mode == INET_MODE_GRAPH) {
+          CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        } else {
+          void* args[] = {&d};
+          CK(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3((unsigned)B), args,
+                                         smem, ctx->stream));
+        }
+        launches++;
+        uint32_t hit = 0;
+        CK(cudaMemcpyAsync(&hit, &ctx->dev.ctrl->hit_slice, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (!hit) break;
+        static const unsigned long long zero8 = 0;
+        CK(cudaMemcpyAsync(&ctx->dev.ctrl->done, &zero8, 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(&ctx->dev.ctrl->hit_slice, &zero8, 4, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(&ctx->dev.ctrl->slice_t0, &zero8, 8, cudaMemcpyHostToDevice, ctx->stream));
+      }
+    }
+  }
+  CK(cudaEventRecord(ctx->ev1, ctx->stream));
+  // results
+  Ctrl hc;
+  CK(cudaMemcpyAsync(&hc, ctx->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<unsigned long long> hist(INET_MAX_RULES);
+  CK(cudaMemcpyAsync(hist.data(), ctx->dev.rule_hist, sizeof(unsigned long long) * INET_MAX_RULES,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  const size_t nn = ctx->nets.size();
+  ctx->h_netctr.resize(nn);
+  ctx->h_netstat.resize(nn);
+  if (nn) {
+    CK(cudaMemcpyAsync(ctx->h_netctr.data(), ctx->dev.netctr, nn * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_netstat.data(), ctx->dev.netstat, nn * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  const uint32_t steps = hc.step - ctx->step;
+  ctx->tr_front.clear();
+  ctx->tr_live.clear();
+  if (o.trace && steps) {
+    const uint32_t k = std::min(steps, kTraceCap);
+    ctx->tr_front.resize(k);
+    ctx->tr_live.resize(k);
+    CK(cudaMemcpyAsync(ctx->tr_front.data(), ctx->dev.trace_front, k * sizeof(long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->tr_live.data(), ctx->dev.trace_live, k * sizeof(long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->step = hc.step;
+  ctx->fcount[0] = hc.fcount[0];
+  ctx->fcount[1] = hc.fcount[1];
+  ctx->a_bump = hc.a_bump;
+  ctx->v_bump = hc.v_bump;
+  ctx->live = hc.live;
+  ctx->st_a0 = ctx->a_bump;
+  ctx->st_v0 = ctx->v_bump;
+  ctx->snap_valid = false;
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    uint64_t tot = 0;
+    for (size_t r = 0; r < ctx->rules.tmpl.size(); r++) {
+      stats->per_rule[r] = hist[r];
+      tot += hist[r];
+    }
+    stats->interactions = tot;
+    stats->steps = steps;
+    stats->max_frontier = hc.max_frontier;
+    stats->live_agents = hc.live;
+    stats->peak_live_agents = std::max<long long>(hc.peak_live, hc.live);
+    stats->pending_pairs = hc.fcount[hc.step & 1u];
+    stats->device_ms = ms;
+    stats->n_rules = (uint32_t)ctx->rules.tmpl.size();
+    // the graph body launches the step kernel once per step
+    if (o.mode == INET_MODE_GRAPH) launches = steps + launches;
+    stats->launches = (uint32_t)std::min<uint64_t>(launches, 0xFFFFFFFFull);
+  }
+  if (hc.fatal) {
+    ctx->poisoned = true;
+    const char* what = hc.fatal == INET_ERR_ARENA_FULL ? "arena, frontier or name capacity exhausted"
+                     : hc.fatal == INET_ERR_TIMEOUT    ? "a device-side wait timed out"
+                                                       : "inconsistent device state";
+    return fail(ctx, hc.fatal, std::string(what) + " (context needs inet_reset)");
+  }
+  if (hc.error == INET_ERR_NO_RULE)
+    return fail(ctx, INET_ERR_NO_RULE, "active pair without a rule in net " + std::to_string(hc.error_info));
+  if (hc.hit_limit) return fail(ctx, INET_ERR_STEP_LIMIT, "step limit reached; call inet_reduce again to continue");
+  return INET_OK;
+}
+
+inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, size_t* needed_out) {
+  if (!ctx) return INET_ERR_INVALID_ARG;
+  inet_status s = check_net(ctx, net_id);
+  if (s) return s;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx))) return s;
+  Readback rb;
+  read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
+           ctx->nets[(size_t)net_id].iface, ctx->rules, (size_t)-1 / 2, true, rb);
+  if (needed_out) *needed_out = rb.text.size() + 1;
+  if (!buf || cap < rb.text.size() + 1) return fail(ctx, INET_ERR_INVALID_ARG, "buffer too small");
+  memcpy(buf, rb.text.c_str(), rb.text.size() + 1);
+  return INET_OK;
+}
+
+inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out, uint64_t* interactions_out) {
+  if (!ctx || !value_out) return INET_ERR_INVALID_ARG;
+  inet_status s = check_net(ctx, net_id);
+  if (s) return s;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx))) return s;
+  Readback rb;
+  read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
+           ctx->nets[(size_t)net_id].iface, ctx->rules, 0, false, rb);
+  if (interactions_out) *interactions_out = ctx->h_netctr[(size_t)net_id] & kNetIntMask;
+  if (rb.nat < 0) return fail(ctx, INET_ERR_INVALID_ARG, "interface is not a numeral S^k(Z)");
+  *value_out = (uint64_t)rb.nat;
+  return INET_OK;
+}
+
+inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out) {
+  if (!ctx || !out) return INET_ERR_INVALID_ARG;
+  inet_status s = check_net(ctx, net_id);
+  if (s) return s;
+  memset(out, 0, sizeof *out);
+  const NetRec& nr = ctx->nets[(size_t)net_id];
+  const unsigned long long v = ctx->h_netctr[(size_t)net_id];
+  out->status = ctx->h_netstat[(size_t)net_id];
+  out->interactions = v & kNetIntMask;
+  out->pending_pairs = v >> kNetPairShift;
+  out->reduced = nr.started && out->pending_pairs == 0 ? 1 : 0;
+  if (ctx->host_only) {
+    out->pending_pairs = nr.pairs.size();
+    return INET_OK;
+  }
+  DeviceGuard g(ctx->device);
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx))) return s;
+  Readback rb;
+  read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(), nr.iface,
+           ctx->rules, 0, false, rb);
+  out->live_agents = (size_t)net_id < ctx->snap_live.size() ? ctx->snap_live[(size_t)net_id] : 0;
+  out->residual_agents = out->live_agents - rb.reached;
+  return INET_OK;
+}
+
+inet_status inet_trace(inet_ctx* ctx, int64_t* frontier, int64_t* live, size_t cap, size_t* n_out) {
+  if (!ctx) return INET_ERR_INVALID_ARG;
+  const size_t k = ctx->tr_front.size();
+  if (n_out) *n_out = k;
+  for (size_t i = 0; i < std::min(k, cap); i++) {
+    if (frontier) frontier[i] = ctx->tr_front[i];
+    if (live) live[i] = ctx->tr_live[i];
+  }
+  return INET_OK;
+}
+
+inet_status inet_reset(inet_ctx* ctx) {
+  if (!ctx) return INET_ERR_INVALID_ARG;
+  ctx->nets.clear();
+  ctx->h_netctr.clear();
+  ctx->h_netstat.clear();
+  ctx->st_nodes.clear();
+  ctx->st_vars.clear();
+  ctx->st_netctr.clear();
+  ctx->a_bump = ctx->v_bump = 0;
+  ctx->st_a0 = ctx->st_v0 = 0;
+  ctx->st_net0 = 0;
+  ctx->live = 0;
+  ctx->step = 0;
+  ctx->fcount[0] = ctx->fcount[1] = 0;
+  ctx->snap_valid = false;
+  ctx->tr_front.clear();
+  ctx->tr_live.clear();
+  ctx->poisoned = false;
+  if (ctx->host_only || !ctx->ws_ready) return INET_OK;
+  DeviceGuard g(ctx->device);
+  return clear_device(ctx);
+}
+
+const char* inet_last_error(const inet_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

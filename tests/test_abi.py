@@ -1,0 +1,156 @@
+"""CPU-only checks of the boundary: the library loads, exports every symbol
+include/inet.h declares, and its host logic (parser, linearity checks, rule
+compiler, net flattener, initial ->com) behaves, through host-only contexts
+that make no CUDA call."""
+import os
+import re
+
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1404_0076_gb300 import build
+    build.build()
+    from paper_1404_0076_gb300 import capi as c
+    return c
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "inet.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(inet_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(capi):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(capi.LIB, n), n
+    assert sorted(capi.EXPORTED) == names
+
+
+def test_workspace_size_grows_with_capacity(capi):
+    small = capi.inet_workspace_bytes(capi.inet_arena_cfg(1000, 1000, 1000, 10, 0))
+    big = capi.inet_workspace_bytes(capi.inet_arena_cfg(10 ** 6, 10 ** 6, 10 ** 5, 1000, 0))
+    assert big - small >= 16 * (10 ** 6 - 1000)
+
+
+def host_ctx(capi):
+    return capi.inet_create(-1, None, None)
+
+
+def test_rule_compiler_shapes(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    assert capi.inet_rule_count(ctx) == 18
+    info = {capi.inet_rule_info(ctx, i)["name"]: capi.inet_rule_info(ctx, i) for i in range(18)}
+    # Eq. (1): +(y,r) = S(x) -> +(y,w) = x, r = S(w): two agents, the name w
+    # joins two auxiliary ports, two equations to link.
+    assert info["Add><S"] == {"name": "Add><S", "arity_alpha": 2, "arity_beta": 1, "n_new": 2,
+                              "new_ports": 3, "n_fresh": 1, "n_link": 2}
+    # Eq. (2): +(y,r) = Z -> r = y: no agent, one equation.
+    assert info["Add><Z"]["n_new"] == 0 and info["Add><Z"]["n_link"] == 1
+    # Fib2><S: Dup, Fib, S, Fib, Add; Fib(w1) = S(a) is itself an active pair.
+    f = info["Fib2><S"]
+    assert (f["n_new"], f["n_fresh"], f["n_link"]) == (5, 2, 2)
+    m = info["Mul><S"]
+    assert (m["n_new"], m["n_fresh"], m["n_link"]) == (3, 2, 2)
+    assert info["Era><Z"]["n_new"] == 0 and info["Era><Z"]["n_link"] == 0
+    capi.inet_destroy(ctx)
+
+
+@pytest.mark.parametrize("text,status", [
+    ("Foo(x) = Bar -> ;", "LINEARITY"),
+    ("Foo(x) = Bar -> x = y;", "LINEARITY"),
+    ("Foo(x, x) = Bar -> x = Bar;", "LINEARITY"),
+    ("Foo(x) = Bar -> x = Bar", "PARSE"),
+    ("Foo(x) = Foo(y) -> x = y;", "PARSE"),
+    ("Foo(x) = Bar -> x = Bar; Foo(y) = Bar -> y = Bar;", "PARSE"),
+    ("Foo(a, b, c, d) = Bar -> a = b, c = d;", "PARSE"),
+    ("Foo(x) = Bar -> x = Bar(Z);", "PARSE"),
+    ("Foo(x) = Bar -> x = $;", "PARSE"),
+])
+def test_rule_errors(capi, text, status):
+    ctx = host_ctx(capi)
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_load_rules(ctx, text)
+    assert e.value.name == status
+    capi.inet_destroy(ctx)
+
+
+@pytest.mark.parametrize("text,status", [
+    ("< r | Add(x, r) = S(x), x = Z >", "LINEARITY"),
+    ("< r | Foo(r) = Z >", "PARSE"),
+    ("< r | Add(r) = Z >", "PARSE"),
+    ("< r | Add(y r) = Z >", "PARSE"),
+    ("< r | Add(y, r) = Z", "PARSE"),
+    ("< r | Add(y, r) = Z > junk", "PARSE"),
+])
+def test_net_errors(capi, text, status):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_load_net(ctx, text)
+    assert e.value.name == status
+    capi.inet_destroy(ctx)
+
+
+def test_initial_com_finds_active_pairs(capi):
+    # Sec. 3.6: {A = x, x = y, y = B} must yield exactly one active pair at
+    # load time; a chain ending in a name yields none.
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, "Alpha = Beta -> ;\n")
+    chain = capi.inet_load_net(ctx, "< | Alpha = x, x = y, y = Beta >")
+    rev = capi.inet_load_net(ctx, "< | y = Beta, x = y, Alpha = x >")
+    open_ = capi.inet_load_net(ctx, "< y | Alpha = x1, x1 = x2, x2 = y >")
+    assert capi.inet_net_info(ctx, chain)["pending_pairs"] == 1
+    assert capi.inet_net_info(ctx, rev)["pending_pairs"] == 1
+    assert capi.inet_net_info(ctx, open_)["pending_pairs"] == 0
+    capi.inet_destroy(ctx)
+
+
+def test_config_nets_load_with_one_pair_each(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    for k in (0, 1, 2, 3):
+        for net in W.CONFIGS[k]().nets[:50]:
+            i = capi.inet_load_net(ctx, net)
+            assert capi.inet_net_info(ctx, i)["pending_pairs"] == 1
+    capi.inet_destroy(ctx)
+
+
+def test_deep_numeral_parses_iteratively(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    i = capi.inet_load_net(ctx, W.add_net(200000, 3))
+    assert capi.inet_net_info(ctx, i)["pending_pairs"] == 1
+    capi.inet_destroy(ctx)
+
+
+def test_host_only_context_refuses_device_work(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    i = capi.inet_load_net(ctx, W.add_net(2, 2))
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_reduce(ctx, [i])
+    assert e.value.name == "NO_DEVICE"
+    with pytest.raises(capi.InetError):
+        capi.inet_readback(ctx, i)
+    capi.inet_destroy(ctx)
+
+
+def test_rules_cannot_change_with_nets_loaded(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    capi.inet_load_net(ctx, W.add_net(1, 1))
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_load_rules(ctx, W.ARITH_RULES)
+    assert e.value.name == "STATE"
+    capi.inet_reset(ctx)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    capi.inet_destroy(ctx)

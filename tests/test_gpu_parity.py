@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA evaluator against the CPU oracle, element by element.
+
+Everything is integer graph rewriting, so the bar is bit-exact: the rendered
+normal form, the numeral value, the interaction count (per net and per rule),
+the live and residual agents of every net, and the per-step frontier sizes
+against the oracle's maximally parallel "rounds" schedule.
+"""
+import json
+import os
+
+import pytest
+
+import workloads as W
+from tests import oracle_runner
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MODES = ["plain", "graph", "persistent"]
+R = W.ARITH_RULES
+
+
+@pytest.fixture(scope="module")
+def orc():
+    oracle_runner.build()
+    return oracle_runner
+
+
+def make_ev(**kw):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_1404_0076_gb300 import Evaluator
+    return Evaluator(device=0, **kw)
+
+
+def run_gpu(rules, nets, mode, text=True, trace=False, **kw):
+    caps = {k: kw.pop(k) for k in ("max_agents", "max_vars", "max_pairs", "max_nets") if k in kw}
+    ev = make_ev(**caps)
+    ev.load_rules(rules)
+    ids = ev.load_nets(nets)
+    st = ev.reduce(ids, mode=mode, trace=trace, **kw)
+    out = []
+    for i in ids:
+        info = ev.net_info(i)
+        rec = {"info": info}
+        if text:
+            rec["result"] = ev.readback(i)
+        try:
+            rec["nat"] = ev.readback_nat(i)[0]
+        except Exception:
+            rec["nat"] = None
+        out.append(rec)
+    tr = ev.trace() if trace else None
+    ev.close()
+    return st, out, tr
+
+
+def compare(oracle_res, gpu_out, text=True):
+    for k, (o, g) in enumerate(zip(oracle_res, gpu_out)):
+        assert o["status"] == "ok", o
+        gi = g["info"]
+        assert gi["status"] == "OK" and gi["reduced"], (k, gi)
+        assert gi["interactions"] == o["interactions"], (k, gi, o["interactions"])
+        assert gi["live_agents"] == o["live"], (k, gi, o["live"])
+        assert gi["residual_agents"] == o["residual_agents"], (k, gi)
+        assert g["nat"] == o["nat"], (k, g["nat"], o["nat"])
+        if text:
+            assert g["result"] == o["result"], (k, g["result"][:200], o["result"][:200])
+
+
+def summed_rounds(oracle_res):
+    L = max((len(o.get("rounds", [])) for o in oracle_res), default=0)
+    agg = [0] * L
+    for o in oracle_res:
+        for i, x in enumerate(o.get("rounds", [])):
+            agg[i] += x
+    return agg
+
+
+def golden():
+    with open(os.path.join(HERE, "golden", "paper_examples.jsonl")) as f:
+        return [json.loads(line) for line in f if line.strip()]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", golden(), ids=lambda c: c["id"])
+def test_paper_examples(orc, mode, case):
+    o = orc.run(case["rules"], case["net"], mode="rounds")
+    st, g, tr = run_gpu(case["rules"], [case["net"]], mode, trace=True)
+    compare(o, g)
+    assert g[0]["result"] == case["expect"]["result"]
+    assert tr[0] == case["expect"]["rounds"]
+
+
+SMALL = ([W.add_net(m, n) for m, n in [(0, 0), (1, 0), (0, 1), (3, 4), (17, 5), (64, 64)]]
+         + [W.mul_net(m, n) for m, n in [(0, 0), (0, 5), (1, 1), (3, 4), (7, 2), (9, 9)]]
+         + [W.ack_net(a, b) for a, b in [(0, 0), (1, 3), (2, 2), (3, 1), (3, 3)]]
+         + [W.fib_net(n) for n in range(0, 13)]
+         + [W.pred_net(n) for n in range(3)]
+         + ["< r | Add(y, r) = S(Z), Add(S(Z), y) = Z >", "< a, b | Dup(a, b) = S(S(Z)) >",
+            "< | >", "< r, s | r = s >", "< S(Z) | >", "< | x = y, y = x >", "< | x = S(y), y = S(x) >",
+            "< r | Add(y, r) = S(S(Z)), y = Add(Z, q), q = Z >"])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_small_mixed_batch(orc, mode):
+    o = orc.run(R, SMALL, mode="rounds")
+    st, g, tr = run_gpu(R, SMALL, mode, trace=True)
+    compare(o, g)
+    assert tr[0] == summed_rounds(o)
+    assert st["interactions"] == sum(x["interactions"] for x in o)
+    per_rule = [sum(x["per_rule"][r] for x in o) for r in range(len(o[0]["per_rule"]))]
+    assert st["per_rule"] == per_rule
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("block", [64, 256, 512])
+def test_several_tiles_and_ragged_tail(orc, mode, block):
+    # 1000 Add nets plus a few wide ones: frontiers of 1000+ pairs over
+    # blocks of 64..512 threads, never a multiple of the block size.
+    nets = [W.add_net((7 * i) % 23, i % 5) for i in range(1000)] + [W.fib_net(11), W.mul_net(6, 5)]
+    o = orc.run(R, nets, mode="rounds", quiet=True)
+    st, g, tr = run_gpu(R, nets, mode, text=False, trace=True, block=block)
+    compare(o, g, text=False)
+    assert tr[0] == summed_rounds(o)
+
+
+@pytest.mark.parametrize("solo_max", [-1, 64, 100000])
+def test_persistent_solo_and_wide(orc, solo_max):
+    nets = [W.fib_net(14), W.ack_net(3, 2), W.mul_net(8, 8)] + [W.add_net(i, 3) for i in range(300)]
+    o = orc.run(R, nets, mode="rounds")
+    st, g, tr = run_gpu(R, nets, "persistent", trace=True, solo_max=solo_max)
+    compare(o, g)
+    assert tr[0] == summed_rounds(o)
+
+
+def full_config(k):
+    w = W.CONFIGS[k]()
+    return w.nets
+
+
+@pytest.mark.parametrize("cfg,mode", [(0, "persistent"), (0, "graph"), (1, "persistent"), (2, "persistent"),
+                                      (3, "persistent"), (2, "graph")])
+def test_full_size_configs(orc, cfg, mode):
+    nets = full_config(cfg)
+    o = orc.run(R, nets, mode="rounds", quiet=(cfg == 1), threads=os.cpu_count() or 4)
+    st, g, tr = run_gpu(R, nets, mode, text=(cfg != 1), trace=True, max_agents=1 << 24, max_vars=1 << 24,
+                        max_pairs=1 << 21)
+    compare(o, g, text=(cfg != 1))
+    assert tr[0] == summed_rounds(o)
+    assert st["interactions"] == sum(x["interactions"] for x in o)
+
+
+def test_plain_loop_fib_and_ack(orc):
+    nets = [W.fib_net(18), W.ack_net(3, 4)]
+    o = orc.run(R, nets, mode="rounds")
+    st, g, tr = run_gpu(R, nets, "plain", trace=True)
+    compare(o, g)
+    assert tr[0] == summed_rounds(o)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_step_limit_is_resumable(orc, mode):
+    net = W.fib_net(13)
+    o = orc.run(R, net)[0]
+    ev = make_ev()
+    ev.load_rules(R)
+    i = ev.load_net(net)
+    st = ev.reduce([i], mode=mode, max_steps=7, check=False)
+    calls = 1
+    while st["status"] == "STEP_LIMIT":
+        assert st["steps"] == 7
+        st = ev.reduce([], mode=mode, max_steps=7, check=False)
+        calls += 1
+    assert st["status"] == "OK" and calls > 3
+    assert ev.readback(i) == o["result"] and ev.net_info(i)["interactions"] == o["interactions"]
+    ev.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_no_rule_stops_only_its_net(orc, mode):
+    rules = R + "Foo(x) = Bar -> x = Bar;\n"
+    nets = [W.add_net(5, 2), "< r | Foo(r) = Z >", W.fib_net(7)]
+    ev = make_ev()
+    ev.load_rules(rules)
+    ids = ev.load_nets(nets)
+    st = ev.reduce(ids, mode=mode, check=False)
+    assert st["status"] == "NO_RULE"
+    assert ev.net_info(ids[1])["status"] == "NO_RULE"
+    o = orc.run(rules, [nets[0], nets[2]])
+    assert ev.readback(ids[0]) == o[0]["result"] and ev.readback(ids[2]) == o[1]["result"]
+    ev.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_arena_full_is_reported_and_reset_recovers(orc, mode):
+    from paper_1404_0076_gb300 import InetError
+    ev = make_ev(max_agents=400, max_vars=400, max_pairs=256)
+    ev.load_rules(R)
+    i = ev.load_net(W.fib_net(12))
+    st = ev.reduce([i], mode=mode, check=False)
+    assert st["status"] == "ARENA_FULL"
+    with pytest.raises(InetError):
+        ev.load_net(W.add_net(1, 1))
+    ev.reset()
+    j = ev.load_net(W.add_net(4, 4))
+    ev.reduce([j], mode=mode)
+    assert ev.readback_nat(j) == (8, 5)
+    ev.close()
+
+
+def test_bounded_wait_times_out_cleanly(orc):
+    # A 1 ns wait limit makes every grid-barrier wait of the persistent
+    # kernel give up: the kernel must return INET_ERR_TIMEOUT, not hang, and
+    # the context must work again after a reset.
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets([W.add_net(200, 1) for _ in range(2000)])
+    st = ev.reduce(ids, mode="persistent", solo_max=-1, timeout_s=1e-9, check=False)
+    assert st["status"] == "TIMEOUT"
+    ev.reset()
+    j = ev.load_net(W.mul_net(3, 3))
+    ev.reduce([j], mode="persistent")
+    assert ev.readback_nat(j)[0] == 9
+    ev.close()
+
+
+def test_incremental_batches_share_the_loop(orc):
+    # Nets added to a running context (after a partial reduction) finish
+    # with the same results as alone.
+    nets_a = [W.fib_net(12), W.mul_net(5, 7)]
+    nets_b = [W.ack_net(2, 3), W.add_net(30, 4)]
+    o = orc.run(R, nets_a + nets_b)
+    ev = make_ev()
+    ev.load_rules(R)
+    ia = ev.load_nets(nets_a)
+    st = ev.reduce(ia, mode="persistent", max_steps=20, check=False)
+    assert st["status"] == "STEP_LIMIT"
+    ib = ev.load_nets(nets_b)
+    ev.reduce(ib, mode="persistent")
+    for k, i in enumerate(ia + ib):
+        assert ev.readback(i) == o[k]["result"]
+        assert ev.net_info(i)["interactions"] == o[k]["interactions"]
+    ev.close()
