@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 interaction-net evaluator.
+
+One step = one whole reduction to normal form (the int/com loop of Sec. 3.6)
+of one batch of synthetic nets.  Default workload: 2048 independent nets
+Mul(S^m Z, S^n Z), m, n ~ U{0..64} (seed 14040076 + 1), reduced by the
+batched persistent kernel; 47 391 647 interactions per step.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload W] [--mode M]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  `value` = interactions per second of device
+time, inputs resident in HBM (nets loaded and staged before the timed
+region, L2 flushed between steps); `e2e` = the same through the public API
+from host text to host results, copies included.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "interactions/sec and HBM-roofline fraction (batched vs plain); p50/p99 latency"
+UNIT = "interactions/s"
+
+
+def workload(name: str, rank: int = 0):
+    """(nets, description, capacities) of a named workload.  Under N ranks
+    each rank reduces its own batch (seed offset by rank): weak scaling."""
+    if name == "mul2048":
+        w = W.config1(seed=W.SEED_BASE + 1 + 1000 * rank)
+        desc = "2048 nets Mul(S^m Z, S^n Z), m,n ~ U{0..64}, seed 14040076+1"
+        caps = dict(max_agents=1 << 24, max_vars=1 << 24, max_pairs=1 << 20, max_nets=4096)
+    elif name == "add4096":
+        w = W.config0(seed=W.SEED_BASE + 0 + 1000 * rank)
+        desc = "4096 nets Add(S^m Z, S^n Z), m,n ~ U{0..256}, seed 14040076"
+        caps = dict(max_agents=1 << 22, max_vars=1 << 22, max_pairs=1 << 20, max_nets=8192)
+    elif name == "ack3":
+        w = W.config2()
+        desc = "5 nets A(S^3 Z, S^b Z), b = 4..8"
+        caps = dict(max_agents=1 << 22, max_vars=1 << 22, max_pairs=1 << 20, max_nets=64)
+    elif name == "fib":
+        w = W.config3()
+        desc = "6 nets Fib(S^n Z), n = 20..25"
+        caps = dict(max_agents=1 << 23, max_vars=1 << 23, max_pairs=1 << 20, max_nets=64)
+    elif name == "fib25x64":
+        w = W.replicated(W.config3(ns=(25,)), 64)
+        desc = "64 copies of Fib(S^25 Z)"
+        caps = dict(max_agents=1 << 25, max_vars=1 << 25, max_pairs=1 << 23, max_nets=128)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w.nets, desc, caps
+
+
+# --- algorithmic bytes per interaction ---------------------------------------------
+# B_r = 8 (pair) + 8 (two labels) + 4 (ar_alpha + ar_beta) (auxiliary words read)
+#     + sum over new agents 4 (1 + ar) (records written) + 4 fresh names
+#     + 8 per equation linked (exchange or pair push) + 4 |new agents - 2|
+#     + 8 when batched (net id with the pair read and with the pair pushed).
+def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
+    out = []
+    for r in rules:
+        b = 8 + 8 + 4 * (r["arity_alpha"] + r["arity_beta"]) + 4 * (r["n_new"] + r["new_ports"])
+        b += 4 * r["n_fresh"] + 8 * r["n_link"] + 4 * abs(r["n_new"] - 2)
+        if batched:
+            b += 8
+        out.append(b)
+    return out
+
+
+# DRAM bytes per launch from ncu captures (profiles/), valid only for the
+# kernel source they were taken on (sha1 prefix of csrc/inet_kernels.cuh).
+NCU_TRAFFIC = {("mul2048", "persistent", "e16f5c9e0bc2"): 37_429_248 + 237_167_616}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    p = os.path.join(ROOT, "paper_1404_0076_gb300", "csrc", "inet_kernels.cuh")
+    with open(p, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --- clocks during the timed region ---------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --- the CPU oracle (cpu_baseline and the reference arm) -----------------------------
+def oracle_binary() -> str:
+    exe = os.path.join(ROOT, "oracle", "inet_oracle")
+    src = os.path.join(ROOT, "oracle", "inet_oracle.cpp")
+    if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
+        subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", src, "-o", exe], check=True)
+    return exe
+
+
+def run_oracle(nets, threads: int):
+    """Times the oracle on the host; returns (interactions, seconds)."""
+    import tempfile
+    exe = oracle_binary()
+    with tempfile.TemporaryDirectory() as d:
+        rp, np_ = os.path.join(d, "r.txt"), os.path.join(d, "n.txt")
+        with open(rp, "w") as f:
+            f.write(W.ARITH_RULES)
+        with open(np_, "w") as f:
+            f.write("\n".join(nets) + "\n")
+        p = subprocess.run([exe, rp, np_, "--quiet", "--threads", str(threads)], capture_output=True, text=True)
+    tail = json.loads(p.stderr.strip().splitlines()[-1])
+    return tail["interactions"], tail["seconds"]
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    nets, desc, _ = workload(args.workload)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        run_oracle(nets, cores)
+    tot_i, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        i, s = run_oracle(nets, cores)
+        tot_i += i
+        tot_s += s
+    value = tot_i / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": desc, "nets": len(nets)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"whole workload per step ({len(nets)} nets), {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --- our arm ------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mul2048")
+    ap.add_argument("--mode", default="persistent", choices=["persistent", "graph", "plain"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--solo-max", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_1404_0076_gb300 import Evaluator
+
+    nets, desc, caps = workload(args.workload, rank)
+    ev = Evaluator(device=local, **caps)
+    ev.load_rules(W.ARITH_RULES)
+    rules = ev.rules()
+    bpr = bytes_per_rule(rules, batched=len(nets) > 1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 129 MB L2
+    opts = dict(mode=args.mode, block=args.block, grid=args.grid, solo_max=args.solo_max)
+
+    def prepared():
+        ev.reset()
+        ids = ev.load_nets(nets)
+        ev.stage(ids)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        return ids
+
+    for _ in range(args.warmup):
+        prepared()
+        ev.reduce([], **opts)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    dev_ms, ints, launches, alg_bytes = [], 0, 0, 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            prepared()
+            st = ev.reduce([], **opts)
+            dev_ms.append(st["device_ms"])
+            ints += st["interactions"]
+            launches += st["launches"]
+            alg_bytes += sum(c * b for c, b in zip(st["per_rule"], bpr))
+    torch.cuda.synchronize()
+    total_s = sum(dev_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s, float(ints)], dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_s_max, ints_all = float(tmax[0]), float(t[1])
+    else:
+        total_s_max, ints_all = total_s, float(ints)
+    value = ints_all / total_s_max
+
+    # roofline of the dominant kernel (the persistent kernel: one launch per step)
+    peak, peak_kind = measured_peaks()
+    launch_s = total_s / max(1, launches)
+    achieved = (alg_bytes / max(1, launches)) / launch_s / 1e9
+    traffic = NCU_TRAFFIC.get((args.workload, args.mode, kernel_source_hash()))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "bytes_per_interaction": alg_bytes / max(1, ints),
+            "kernel": {"persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[args.mode]}
+
+    # e2e: public API from host text to host results, copies included
+    e2e_ms, e2e_h2d, e2e_d2h, e2e_int = [], 0, 0, 0
+    for _ in range(args.e2e_steps):
+        ev.reset()
+        torch.cuda.synchronize()
+        h0, d0 = ev.transfer_bytes()
+        t0 = time.perf_counter()
+        ids = ev.load_nets(nets)
+        st = ev.reduce(ids, **opts)
+        vals = [ev.readback_nat(i) for i in ids]
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        h1, d1 = ev.transfer_bytes()
+        e2e_h2d, e2e_d2h = h1 - h0, d1 - d0
+        e2e_int = sum(v[1] for v in vals)
+    e2e = {"value": e2e_int / (statistics.median(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
+           "ms_per_step": statistics.median(e2e_ms)}
+
+    # the plain host-driven loop: whole batch, and one net per launch sequence
+    plain = None
+    if not args.no_plain and rank == 0:
+        ids = prepared()
+        stp = ev.reduce([], mode="plain")
+        one = []
+        sample = nets[:16]
+        for net in sample:
+            ev.reset()
+            i = ev.load_net(net)
+            ev.stage([i])
+            torch.cuda.synchronize()
+            s1 = ev.reduce([], mode="plain")
+            one.append((s1["interactions"], s1["device_ms"]))
+        plain = {"batch_plain": stp["interactions"] / (stp["device_ms"] / 1e3),
+                 "one_net_per_launch": sum(a for a, _ in one) / (sum(b for _, b in one) / 1e3),
+                 "one_net_sample": f"first {len(sample)} nets, each reduced alone by the host-driven loop",
+                 "unit": UNIT}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        ci, cs = run_oracle(nets, cores)
+        cpu = {"value": ci / cs, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"whole workload once ({len(nets)} nets, {ci} interactions), {cores} threads"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": desc, "nets_per_rank": len(nets), "interactions_per_step": ints // args.steps,
+                           "mode": args.mode, "block": args.block or 256, "grid": args.grid or "auto",
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "parallelism": f"independent batches, {world} rank(s)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "plain": plain}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ev.close()
+
+
+if __name__ == "__main__":
+    main()

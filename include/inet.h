@@ -164,13 +164,23 @@ inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len);
 inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* net_id_out);
 
 /* Adds the active pairs of the listed nets (which must not have been
- * reduced yet; n may be 0) to the frontier and runs the reduction loop of
+ * staged or reduced yet; n may be 0) to the frontier and runs the reduction loop of
  * Sec. 3.6 until no active pair remains in the whole context, an error
  * occurs, or opts->max_steps steps have run.  opts and stats may be NULL.
  * Per-net errors (NO_RULE) do not stop other nets; the first error is
  * returned. */
 inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
                         const inet_reduce_opts* opts, inet_reduce_stats* stats);
+
+/* Admission without running: uploads loaded nets and adds the active pairs
+ * of the listed nets (not yet staged or reduced) to the device frontier.
+ * A later inet_reduce(ctx, NULL, 0, ...) reduces them together with any
+ * pairs already in flight. */
+inet_status inet_stage(inet_ctx* ctx, const int32_t* net_ids, int32_t n);
+
+/* Total bytes this context has copied host-to-device and device-to-host
+ * (either pointer may be NULL). */
+inet_status inet_transfer_bytes(const inet_ctx* ctx, uint64_t* h2d_out, uint64_t* d2h_out);
 
 /* Writes the net's interface after ->col and ->sub (Sec. 2.2; Theorem 1),
  * terms left to right, names renamed x0, x1, .. in order of first

@@ -101,6 +101,12 @@ class Evaluator:
                 "device_ms": st.device_ms, "launches": st.launches,
                 "per_rule": list(st.per_rule[:st.n_rules])}
 
+    def stage(self, net_ids) -> None:
+        capi_lazy.inet_stage(self.ctx, list(net_ids))
+
+    def transfer_bytes(self) -> tuple[int, int]:
+        return capi_lazy.inet_transfer_bytes(self.ctx)
+
     def readback(self, net_id: int) -> str:
         return capi_lazy.inet_readback(self.ctx, net_id)
 

@@ -38,8 +38,8 @@ INET_MAX_RULES = 64
 EXPORTED = [
     "inet_workspace_bytes", "inet_create", "inet_attach_workspace", "inet_destroy",
     "inet_load_rules", "inet_rule_count", "inet_rule_info", "inet_load_net", "inet_reduce",
-    "inet_readback", "inet_readback_nat", "inet_net_info", "inet_trace", "inet_reset",
-    "inet_last_error",
+    "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
+    "inet_trace", "inet_reset", "inet_last_error",
 ]
 
 
@@ -95,6 +95,8 @@ def _load():
         "inet_load_net": ([P, C.c_char_p, C.c_size_t, C.POINTER(C.c_int32)], C.c_int32),
         "inet_reduce": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(inet_reduce_opts),
                          C.POINTER(inet_reduce_stats)], C.c_int32),
+        "inet_stage": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
+        "inet_transfer_bytes": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
         "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_net_info": ([P, C.c_int32, C.POINTER(inet_net_stats)], C.c_int32),
@@ -181,6 +183,18 @@ def inet_reduce(ctx, net_ids, opts: inet_reduce_opts | None = None, check: bool 
         err.stats = st
         raise err
     return rc, st
+
+
+def inet_stage(ctx, net_ids) -> None:
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    _check(ctx, LIB.inet_stage(ctx, ids, len(net_ids)))
+
+
+def inet_transfer_bytes(ctx) -> tuple[int, int]:
+    a = C.c_uint64()
+    b = C.c_uint64()
+    _check(ctx, LIB.inet_transfer_bytes(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def inet_readback(ctx, net_id: int) -> str:

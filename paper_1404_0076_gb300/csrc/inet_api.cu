@@ -123,6 +123,7 @@ struct inet_ctx {
   // trace of the last reduce
   std::vector<long long> tr_front, tr_live;
   bool poisoned = false;
+  uint64_t h2d_bytes = 0, d2h_bytes = 0;  // host<->device bytes copied by this context
   std::string err;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -154,6 +155,15 @@ inet_status fail(inet_ctx* c, inet_status code, const std::string& msg) {
       return fail(ctx, INET_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     }                                                                                     \
   } while (0)
+
+cudaError_t h2d(inet_ctx* ctx, void* dst, const void* src, size_t n) {
+  ctx->h2d_bytes += n;
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, ctx->stream);
+}
+cudaError_t d2h(inet_ctx* ctx, void* dst, const void* src, size_t n) {
+  ctx->d2h_bytes += n;
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, ctx->stream);
+}
 
 template <class T>
 T* at(inet_ctx* ctx, size_t off) {
@@ -198,12 +208,10 @@ inet_status upload_rules(inet_ctx* ctx) {
   std::vector<uint8_t> ar(kMaxLabels, 0);
   for (size_t i = 0; i < r.arity.size(); i++) ar[i] = (uint8_t)r.arity[i];
   if (!r.table.empty())
-    CK(cudaMemcpyAsync(ctx->ws + ctx->lay.table, r.table.data(), r.table.size() * sizeof(int16_t),
-                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->ws + ctx->lay.table, r.table.data(), r.table.size() * sizeof(int16_t)));
   if (!r.tmpl.empty())
-    CK(cudaMemcpyAsync(ctx->ws + ctx->lay.tmpl, r.tmpl.data(), r.tmpl.size() * sizeof(Template),
-                       cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->ws + ctx->lay.arity, ar.data(), kMaxLabels, cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->ws + ctx->lay.tmpl, r.tmpl.data(), r.tmpl.size() * sizeof(Template)));
+  CK(h2d(ctx, ctx->ws + ctx->lay.arity, ar.data(), kMaxLabels));
   CK(cudaStreamSynchronize(ctx->stream));
   fill_dev(ctx);
   return INET_OK;
@@ -217,7 +225,7 @@ inet_status clear_device(inet_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netstat, 0, sizeof(int32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
   uint32_t never = 0xFFFFFFFFu;
-  CK(cudaMemcpyAsync(&ctx->dev.ctrl->stop_step, &never, 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(h2d(ctx, &ctx->dev.ctrl->stop_step, &never, 4));
   CK(cudaStreamSynchronize(ctx->stream));
   return INET_OK;
 }
@@ -241,14 +249,12 @@ inet_status ensure_workspace(inet_ctx* ctx) {
 // Copies staged nets to the device and the host-side counters to the control block.
 inet_status upload_staged(inet_ctx* ctx) {
   if (!ctx->st_nodes.empty())
-    CK(cudaMemcpyAsync(ctx->dev.node + ctx->st_a0, ctx->st_nodes.data(), ctx->st_nodes.size() * sizeof(Node),
-                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->dev.node + ctx->st_a0, ctx->st_nodes.data(), ctx->st_nodes.size() * sizeof(Node)));
   if (!ctx->st_vars.empty())
-    CK(cudaMemcpyAsync(ctx->dev.var + ctx->st_v0, ctx->st_vars.data(), ctx->st_vars.size() * sizeof(uint32_t),
-                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->dev.var + ctx->st_v0, ctx->st_vars.data(), ctx->st_vars.size() * sizeof(uint32_t)));
   if (!ctx->st_netctr.empty()) {
-    CK(cudaMemcpyAsync(ctx->dev.netctr + ctx->st_net0, ctx->st_netctr.data(),
-                       ctx->st_netctr.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->dev.netctr + ctx->st_net0, ctx->st_netctr.data(),
+                       ctx->st_netctr.size() * sizeof(unsigned long long)));
     CK(cudaMemsetAsync(ctx->dev.netstat + ctx->st_net0, 0, ctx->st_netctr.size() * sizeof(int32_t), ctx->stream));
   }
   const bool any = !ctx->st_nodes.empty() || !ctx->st_vars.empty() || !ctx->st_netctr.empty();
@@ -258,9 +264,9 @@ inet_status upload_staged(inet_ctx* ctx) {
     hb[0] = ctx->a_bump;
     hb[1] = ctx->v_bump;
     hl = ctx->live;
-    CK(cudaMemcpyAsync(&ctx->dev.ctrl->a_bump, &hb[0], 8, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(&ctx->dev.ctrl->v_bump, &hb[1], 8, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(&ctx->dev.ctrl->live, &hl, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, &ctx->dev.ctrl->a_bump, &hb[0], 8));
+    CK(h2d(ctx, &ctx->dev.ctrl->v_bump, &hb[1], 8));
+    CK(h2d(ctx, &ctx->dev.ctrl->live, &hl, 8));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   ctx->st_nodes.clear();
@@ -269,7 +275,7 @@ inet_status upload_staged(inet_ctx* ctx) {
   ctx->st_a0 = ctx->a_bump;
   ctx->st_v0 = ctx->v_bump;
   ctx->st_net0 = (uint32_t)ctx->nets.size();
-  ctx->snap_valid = false;
+  if (any) ctx->snap_valid = false;
   return INET_OK;
 }
 
@@ -322,13 +328,11 @@ inet_status ensure_snapshot(inet_ctx* ctx) {
   ctx->snap_nodes.resize(ctx->a_bump);
   ctx->snap_vars.resize(ctx->v_bump);
   if (ctx->a_bump)
-    CK(cudaMemcpyAsync(ctx->snap_nodes.data(), ctx->dev.node, ctx->a_bump * sizeof(Node), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(d2h(ctx, ctx->snap_nodes.data(), ctx->dev.node, ctx->a_bump * sizeof(Node)));
   if (ctx->v_bump)
-    CK(cudaMemcpyAsync(ctx->snap_vars.data(), ctx->dev.var, ctx->v_bump * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(d2h(ctx, ctx->snap_vars.data(), ctx->dev.var, ctx->v_bump * sizeof(uint32_t)));
   Ctrl hc;
-  CK(cudaMemcpyAsync(&hc, ctx->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(d2h(ctx, &hc, ctx->dev.ctrl, sizeof(Ctrl)));
   CK(cudaStreamSynchronize(ctx->stream));
   // free agent slots: ring entries [a_head, a_tail)
   std::vector<uint8_t> is_free(ctx->a_bump, 0);
@@ -338,10 +342,9 @@ inet_status ensure_snapshot(inet_ctx* ctx) {
     std::vector<uint32_t> ring(nfree);
     uint64_t h = hc.a_head % cap;
     uint64_t first = std::min<uint64_t>(nfree, cap - h);
-    CK(cudaMemcpyAsync(ring.data(), ctx->dev.afree + h, first * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(d2h(ctx, ring.data(), ctx->dev.afree + h, first * 4));
     if (nfree > first)
-      CK(cudaMemcpyAsync(ring.data() + first, ctx->dev.afree, (nfree - first) * 4, cudaMemcpyDeviceToHost,
-                         ctx->stream));
+      CK(d2h(ctx, ring.data() + first, ctx->dev.afree, (nfree - first) * 4));
     CK(cudaStreamSynchronize(ctx->stream));
     for (uint32_t s : ring)
       if (s < ctx->a_bump) is_free[s] = 1;
@@ -359,6 +362,40 @@ inet_status ensure_snapshot(inet_ctx* ctx) {
 inet_status check_net(inet_ctx* ctx, int32_t id) {
   if (id < 0 || (size_t)id >= ctx->nets.size() || !ctx->nets[(size_t)id].used)
     return fail(ctx, INET_ERR_INVALID_ARG, "unknown net id " + std::to_string(id));
+  return INET_OK;
+}
+
+// Uploads staged nets and appends the initial active pairs of the listed
+// nets to the current frontier on the device.
+inet_status stage_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
+  for (int32_t i = 0; i < n; i++) {
+    inet_status s = check_net(ctx, net_ids[i]);
+    if (s) return s;
+    if (ctx->nets[(size_t)net_ids[i]].started) return fail(ctx, INET_ERR_INVALID_ARG, "net already staged or reduced");
+  }
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  s = upload_staged(ctx);
+  if (s) return s;
+  std::vector<Pair> add;
+  for (int32_t i = 0; i < n; i++) {
+    const NetRec& nr = ctx->nets[(size_t)net_ids[i]];
+    add.insert(add.end(), nr.pairs.begin(), nr.pairs.end());
+  }
+  const uint32_t cur = ctx->step & 1u;
+  if ((uint64_t)ctx->fcount[cur] + add.size() > ctx->cfg.max_pairs)
+    return fail(ctx, INET_ERR_ARENA_FULL, "frontier capacity exceeded");
+  for (int32_t i = 0; i < n; i++) {
+    NetRec& nr = ctx->nets[(size_t)net_ids[i]];
+    nr.pairs.clear();
+    nr.pairs.shrink_to_fit();
+    nr.started = true;
+  }
+  if (add.empty()) return INET_OK;
+  CK(h2d(ctx, ctx->dev.front[cur] + ctx->fcount[cur], add.data(), add.size() * sizeof(Pair)));
+  ctx->fcount[cur] += (uint32_t)add.size();
+  CK(h2d(ctx, &ctx->dev.ctrl->fcount[cur], &ctx->fcount[cur], 4));
+  CK(cudaStreamSynchronize(ctx->stream));
   return INET_OK;
 }
 
@@ -532,31 +569,10 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   const int B = o.block ? o.block : 256;
   if (B < 64 || B > 512 || B % 32) return fail(ctx, INET_ERR_INVALID_ARG, "block must be a multiple of 32 in [64, 512]");
   if (o.mode < INET_MODE_PLAIN || o.mode > INET_MODE_PERSISTENT) return fail(ctx, INET_ERR_INVALID_ARG, "bad mode");
-  for (int32_t i = 0; i < n; i++) {
-    inet_status s = check_net(ctx, net_ids[i]);
-    if (s) return s;
-    if (ctx->nets[(size_t)net_ids[i]].started) return fail(ctx, INET_ERR_INVALID_ARG, "net already reduced");
-  }
   DeviceGuard g(ctx->device);
-  inet_status s = ensure_workspace(ctx);
+  inet_status s = stage_nets(ctx, net_ids, n);
   if (s) return s;
-  s = upload_staged(ctx);
-  if (s) return s;
-  // new active pairs join the current frontier
-  std::vector<Pair> add;
-  for (int32_t i = 0; i < n; i++) {
-    NetRec& nr = ctx->nets[(size_t)net_ids[i]];
-    add.insert(add.end(), nr.pairs.begin(), nr.pairs.end());
-    nr.pairs.clear();
-    nr.pairs.shrink_to_fit();
-    nr.started = true;
-  }
   const uint32_t cur = ctx->step & 1u;
-  if ((uint64_t)ctx->fcount[cur] + add.size() > ctx->cfg.max_pairs)
-    return fail(ctx, INET_ERR_ARENA_FULL, "frontier capacity exceeded");
-  if (!add.empty())
-    CK(cudaMemcpyAsync(ctx->dev.front[cur] + ctx->fcount[cur], add.data(), add.size() * sizeof(Pair),
-                       cudaMemcpyHostToDevice, ctx->stream));
   // per-call control fields
   struct {
     uint32_t step, done;
@@ -575,10 +591,8 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   head.trace_on = o.trace ? 1u : 0u;
   head.call_step0 = ctx->step;
   head.peak_live = ctx->live;
-  uint32_t fc[2] = {ctx->fcount[0], ctx->fcount[1]};
-  fc[cur] += (uint32_t)add.size();
-  CK(cudaMemcpyAsync(ctx->dev.ctrl, &head, sizeof head, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->dev.ctrl->fcount, fc, sizeof fc, cudaMemcpyHostToDevice, ctx->stream));
+  const uint32_t fc[2] = {ctx->fcount[0], ctx->fcount[1]};
+  CK(h2d(ctx, ctx->dev.ctrl, &head, sizeof head));
   CK(cudaMemsetAsync(ctx->dev.rule_hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
   Dev d = ctx->dev;
   d.timeout_ns = o.timeout_ns ? o.timeout_ns : kDefaultTimeoutNs;
@@ -596,10 +610,11 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
         k_step<<<grid, B, smem, ctx->stream>>>(d);
         CK(cudaGetLastError());
         launches++;
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
         uint32_t st[4];  // step, done, error, error_info
         uint32_t fcn[2];
-        CK(cudaMemcpyAsync(st, ctx->dev.ctrl, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaMemcpyAsync(fcn, ctx->dev.ctrl->fcount, sizeof fcn, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(d2h(ctx, st, ctx->dev.ctrl, sizeof st));
+        CK(d2h(ctx, fcn, ctx->dev.ctrl->fcount, sizeof fcn));
         CK(cudaStreamSynchronize(ctx->stream));
         if (st[1]) break;
         pending = fcn[st[0] & 1u];
@@ -633,32 +648,30 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
                                          smem, ctx->stream));
         }
         launches++;
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
         uint32_t hit = 0;
-        CK(cudaMemcpyAsync(&hit, &ctx->dev.ctrl->hit_slice, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(d2h(ctx, &hit, &ctx->dev.ctrl->hit_slice, 4));
         CK(cudaStreamSynchronize(ctx->stream));
         if (!hit) break;
         static const unsigned long long zero8 = 0;
-        CK(cudaMemcpyAsync(&ctx->dev.ctrl->done, &zero8, 4, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(&ctx->dev.ctrl->hit_slice, &zero8, 4, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(&ctx->dev.ctrl->slice_t0, &zero8, 8, cudaMemcpyHostToDevice, ctx->stream));
+        CK(h2d(ctx, &ctx->dev.ctrl->done, &zero8, 4));
+        CK(h2d(ctx, &ctx->dev.ctrl->hit_slice, &zero8, 4));
+        CK(h2d(ctx, &ctx->dev.ctrl->slice_t0, &zero8, 8));
       }
     }
   }
-  CK(cudaEventRecord(ctx->ev1, ctx->stream));
+  if (!launches) CK(cudaEventRecord(ctx->ev1, ctx->stream));
   // results
   Ctrl hc;
-  CK(cudaMemcpyAsync(&hc, ctx->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(d2h(ctx, &hc, ctx->dev.ctrl, sizeof(Ctrl)));
   std::vector<unsigned long long> hist(INET_MAX_RULES);
-  CK(cudaMemcpyAsync(hist.data(), ctx->dev.rule_hist, sizeof(unsigned long long) * INET_MAX_RULES,
-                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(d2h(ctx, hist.data(), ctx->dev.rule_hist, sizeof(unsigned long long) * INET_MAX_RULES));
   const size_t nn = ctx->nets.size();
   ctx->h_netctr.resize(nn);
   ctx->h_netstat.resize(nn);
   if (nn) {
-    CK(cudaMemcpyAsync(ctx->h_netctr.data(), ctx->dev.netctr, nn * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_netstat.data(), ctx->dev.netstat, nn * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(d2h(ctx, ctx->h_netctr.data(), ctx->dev.netctr, nn * sizeof(unsigned long long)));
+    CK(d2h(ctx, ctx->h_netstat.data(), ctx->dev.netstat, nn * sizeof(int32_t)));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   float ms = 0;
@@ -670,10 +683,8 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
     const uint32_t k = std::min(steps, kTraceCap);
     ctx->tr_front.resize(k);
     ctx->tr_live.resize(k);
-    CK(cudaMemcpyAsync(ctx->tr_front.data(), ctx->dev.trace_front, k * sizeof(long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(ctx->tr_live.data(), ctx->dev.trace_live, k * sizeof(long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(d2h(ctx, ctx->tr_front.data(), ctx->dev.trace_front, k * sizeof(long long)));
+    CK(d2h(ctx, ctx->tr_live.data(), ctx->dev.trace_live, k * sizeof(long long)));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   ctx->step = hc.step;
@@ -714,6 +725,21 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   if (hc.error == INET_ERR_NO_RULE)
     return fail(ctx, INET_ERR_NO_RULE, "active pair without a rule in net " + std::to_string(hc.error_info));
   if (hc.hit_limit) return fail(ctx, INET_ERR_STEP_LIMIT, "step limit reached; call inet_reduce again to continue");
+  return INET_OK;
+}
+
+inet_status inet_stage(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
+  if (!ctx || n < 0 || (n > 0 && !net_ids)) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  DeviceGuard g(ctx->device);
+  return stage_nets(ctx, net_ids, n);
+}
+
+inet_status inet_transfer_bytes(const inet_ctx* ctx, uint64_t* h2d_out, uint64_t* d2h_out) {
+  if (!ctx) return INET_ERR_INVALID_ARG;
+  if (h2d_out) *h2d_out = ctx->h2d_bytes;
+  if (d2h_out) *d2h_out = ctx->d2h_bytes;
   return INET_OK;
 }
 
