@@ -206,6 +206,42 @@ inet_status inet_trace(inet_ctx* ctx, int64_t* frontier, int64_t* live, size_t c
  * Clears a poisoned state. */
 inet_status inet_reset(inet_ctx* ctx);
 
+/* ---- Reduction without any allocation ------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate on their request path: a serving process whose allocator
+ * reserved all GPU memory at start-up, or code with a hard latency budget
+ * where cudaMalloc (and the synchronisation it implies) is not allowed.
+ *
+ * It reduces net `net_id` of a HOST-ONLY context (inet_create with device
+ * < 0, rules and nets loaded there ahead of time; that set-up may allocate)
+ * on CUDA device `device`, on `stream` (NULL: the legacy default stream),
+ * and calls no cudaMalloc, cudaFree or other allocating routine:
+ *   - `arena` is caller-owned device memory, 256-byte aligned, of at least
+ *     round_up(16 * max_agents, 256) + 4 * max_vars bytes: agent records
+ *     first, then name slots.  Every net of the context is copied there at
+ *     the start of the call (agent ids from 0); on return it holds the
+ *     normal form.
+ *   - The frontier, the free-slot rings, the control block, the rule tables
+ *     and the per-net counters live in one fixed array of
+ *     INET_FIXED_SCRATCH_BYTES in device memory, which every GPU that loads
+ *     the library holds until the process exits.  Hence the limits:
+ *     max_agents and max_vars <= 1048576, at most 262144 active pairs in a
+ *     step, at most 4096 nets in the context.  Larger sizes are rejected
+ *     with INET_ERR_INVALID_ARG before any device work.
+ *   - The first call on a device looks the array's address up on that
+ *     device (cudaGetSymbolAddress); make that first call before any stream
+ *     capture begins.
+ *   - All calls on a device share the array, and each call clears what must
+ *     start at zero.  Calls that overlap on the GPU race: issue them one at
+ *     a time (the call returns only after its device work is finished).
+ * On success *value_out is k when the net's interface is the numeral S^k(Z)
+ * (otherwise INET_ERR_INVALID_ARG) and *interactions_out (may be NULL) the
+ * number of interactions. */
+#define INET_FIXED_SCRATCH_BYTES 12647168u
+inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void* arena, size_t arena_bytes,
+                             uint64_t max_agents, uint64_t max_vars, int device, void* stream,
+                             uint64_t* value_out, uint64_t* interactions_out);
+
 /* Message of the last failed call on this context (never NULL). */
 const char* inet_last_error(const inet_ctx* ctx);
 

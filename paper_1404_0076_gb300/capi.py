@@ -39,7 +39,7 @@ EXPORTED = [
     "inet_workspace_bytes", "inet_create", "inet_attach_workspace", "inet_destroy",
     "inet_load_rules", "inet_rule_count", "inet_rule_info", "inet_load_net", "inet_reduce",
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
-    "inet_trace", "inet_reset", "inet_last_error",
+    "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into",
 ]
 
 
@@ -104,6 +104,8 @@ def _load():
                        C.c_int32),
         "inet_reset": ([P], C.c_int32),
         "inet_last_error": ([P], C.c_char_p),
+        "inet_reduce_into": ([P, C.c_int32, P, C.c_size_t, C.c_uint64, C.c_uint64, C.c_int, P,
+                              C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -233,6 +235,18 @@ def inet_trace(ctx) -> tuple[list[int], list[int]]:
 
 def inet_reset(ctx) -> None:
     _check(ctx, LIB.inet_reset(ctx))
+
+
+def inet_reduce_into(host_ctx, net_id: int, arena_ptr: int, arena_bytes: int, max_agents: int,
+                     max_vars: int, device: int, stream: int | None = None) -> tuple[int, int]:
+    """Reduces a net of a host-only context inside caller-owned device memory
+    without allocating anything; returns (numeral value, interactions)."""
+    v = C.c_uint64()
+    n = C.c_uint64()
+    _check(host_ctx, LIB.inet_reduce_into(host_ctx, net_id, C.c_void_p(arena_ptr), arena_bytes, max_agents,
+                                          max_vars, device, C.c_void_p(stream) if stream else None,
+                                          C.byref(v), C.byref(n)))
+    return v.value, n.value
 
 
 def inet_last_error(ctx) -> str:

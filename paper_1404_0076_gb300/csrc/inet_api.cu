@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -840,3 +841,231 @@ const char* inet_last_error(const inet_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry point that allocates no memory, for callers that cannot call
+// cudaMalloc or any allocator on their request path: a serving process whose
+// allocator has already reserved the whole GPU at start-up, or code with a
+// hard latency budget where a device allocation (and its implicit
+// synchronisation) is not allowed.  The caller owns the arena that holds the
+// net; everything else the reduction needs (frontier buffers, free-slot
+// rings, control block, rule tables, per-net counters) lives in one fixed
+// array in device memory, below, which every GPU that loads this library
+// keeps until the process exits.
+
+namespace {
+
+constexpr uint64_t kFixedAgents = 1ull << 20;   // agent slots the fixed rings can recycle
+constexpr uint64_t kFixedVars = 1ull << 20;     // name slots
+constexpr uint32_t kFixedPairs = 1u << 18;      // frontier capacity (each of two buffers)
+constexpr uint32_t kFixedNets = 4096;           // nets the host-only context may hold
+
+constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kFxCtrl = 0;
+constexpr size_t kFxTable = up256(kFxCtrl + sizeof(Ctrl));
+constexpr size_t kFxTmpl = up256(kFxTable + sizeof(int16_t) * kMaxLabels * kMaxLabels);
+constexpr size_t kFxArity = up256(kFxTmpl + sizeof(Template) * INET_MAX_RULES);
+constexpr size_t kFxHist = up256(kFxArity + kMaxLabels);
+constexpr size_t kFxNetctr = up256(kFxHist + sizeof(unsigned long long) * INET_MAX_RULES);
+constexpr size_t kFxNetstat = up256(kFxNetctr + sizeof(unsigned long long) * kFixedNets);
+constexpr size_t kFxFront0 = up256(kFxNetstat + sizeof(int32_t) * kFixedNets);
+constexpr size_t kFxFront1 = up256(kFxFront0 + sizeof(Pair) * kFixedPairs);
+constexpr size_t kFxAfree = up256(kFxFront1 + sizeof(Pair) * kFixedPairs);
+constexpr size_t kFxVfree = up256(kFxAfree + sizeof(uint32_t) * kFixedAgents);
+constexpr size_t kFxOut = up256(kFxVfree + sizeof(uint32_t) * kFixedVars);
+constexpr size_t kFixedBytes = up256(kFxOut + 64);
+static_assert(kFixedBytes == INET_FIXED_SCRATCH_BYTES, "fixed scratch size in inet.h is out of date");
+
+}  // namespace
+
+// The fixed scratch array.  Host code must not use this name as an address:
+// it is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress() below.
+static __device__ __align__(256) unsigned char g_inet_fixed_scratch[kFixedBytes];
+
+namespace {
+
+std::mutex g_fixed_mu;
+void* g_fixed_addr[256] = {};
+
+// Device address of the fixed scratch on `device`, looked up once per device
+// with that device current.
+inet_status fixed_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_fixed_mu);
+  if (device < 0 || device >= 256) return INET_ERR_INVALID_ARG;
+  if (!g_fixed_addr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_inet_fixed_scratch) != cudaSuccess || !p) return INET_ERR_CUDA;
+    g_fixed_addr[device] = p;
+  }
+  *out = g_fixed_addr[device];
+  return INET_OK;
+}
+
+// Reads the numeral S^k(Z) at the interface word `root` (one thread; name
+// slots are followed as ->col/->sub do).  out[0] = k or -1.
+__global__ void k_fixed_read_nat(const Node* nodes, const uint32_t* vars, uint64_t n_agents, uint64_t n_vars,
+                                 uint32_t root, int s_label, int z_label, long long* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long k = 0;
+  uint32_t w = root;
+  for (uint64_t guard = 0; guard <= n_agents + n_vars; guard++) {
+    if (is_var(w)) {
+      const uint32_t x = idx_of(w);
+      if (x >= n_vars) break;
+      const uint32_t v = __ldcg(vars + x);
+      if (v == kEmpty) break;
+      w = v;
+      continue;
+    }
+    if (!is_agent(w) || idx_of(w) >= n_agents) break;
+    const int4 r = __ldcg(reinterpret_cast<const int4*>(nodes + idx_of(w)));
+    const int lab = r.x & 0xFF;
+    if (lab == z_label) {
+      out[0] = k;
+      return;
+    }
+    if (lab != s_label) break;
+    k++;
+    w = (uint32_t)r.y;
+  }
+  out[0] = -1;
+}
+
+}  // namespace
+
+extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void* arena, size_t arena_bytes,
+                                        uint64_t max_agents, uint64_t max_vars, int device, void* stream,
+                                        uint64_t* value_out, uint64_t* interactions_out) {
+  inet_ctx* ctx = host_ctx;
+  if (!ctx || !arena || !value_out) return INET_ERR_INVALID_ARG;
+  if (!ctx->host_only) return fail(ctx, INET_ERR_INVALID_ARG, "inet_reduce_into takes a host-only context");
+  if (!ctx->have_rules) return fail(ctx, INET_ERR_STATE, "load rules first");
+  inet_status s = check_net(ctx, net_id);
+  if (s) return s;
+  const NetRec& nr = ctx->nets[(size_t)net_id];
+  const size_t var_off = up256(sizeof(Node) * max_agents);
+  if (max_agents > kFixedAgents || max_vars > kFixedVars)
+    return fail(ctx, INET_ERR_INVALID_ARG, "max_agents and max_vars may not exceed 1048576 (fixed scratch limit)");
+  if (ctx->nets.size() > kFixedNets)
+    return fail(ctx, INET_ERR_INVALID_ARG, "the host-only context holds more than 4096 nets (fixed scratch limit)");
+  if (nr.pairs.size() > kFixedPairs)
+    return fail(ctx, INET_ERR_INVALID_ARG, "net has more initial active pairs than the fixed frontier holds");
+  if (ctx->st_nodes.size() > max_agents || ctx->st_vars.size() > max_vars)
+    return fail(ctx, INET_ERR_INVALID_ARG, "the context's nets do not fit max_agents / max_vars");
+  if (arena_bytes < var_off + sizeof(uint32_t) * max_vars || (reinterpret_cast<uintptr_t>(arena) & 255))
+    return fail(ctx, INET_ERR_INVALID_ARG, "arena smaller than 16*max_agents (rounded to 256) + 4*max_vars, or not 256-byte aligned");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(ctx, INET_ERR_NO_DEVICE, "no such CUDA device");
+  DeviceGuard g(device);
+  unsigned char* fx = nullptr;
+  s = fixed_scratch(device, reinterpret_cast<void**>(&fx));
+  if (s) return fail(ctx, s, "cudaGetSymbolAddress of the fixed scratch failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Node* nodes = static_cast<Node*>(arena);
+  uint32_t* vars = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(arena) + var_off);
+  const CompiledRules& r = ctx->rules;
+#define FX(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(ctx, INET_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+  // inputs: the context's staged nets (agent ids start at 0) into the arena
+  if (!ctx->st_nodes.empty())
+    FX(cudaMemcpyAsync(nodes, ctx->st_nodes.data(), sizeof(Node) * ctx->st_nodes.size(), cudaMemcpyHostToDevice, st));
+  if (!ctx->st_vars.empty())
+    FX(cudaMemcpyAsync(vars, ctx->st_vars.data(), sizeof(uint32_t) * ctx->st_vars.size(), cudaMemcpyHostToDevice, st));
+  if (max_vars > ctx->st_vars.size())
+    FX(cudaMemsetAsync(vars + ctx->st_vars.size(), 0, sizeof(uint32_t) * (max_vars - ctx->st_vars.size()), st));
+  // scratch: what must start at zero, then the rule tables and the frontier
+  FX(cudaMemsetAsync(fx + kFxHist, 0, kFxFront0 - kFxHist, st));
+  FX(cudaMemcpyAsync(fx + kFxTable, r.table.data(), sizeof(int16_t) * r.table.size(), cudaMemcpyHostToDevice, st));
+  FX(cudaMemcpyAsync(fx + kFxTmpl, r.tmpl.data(), sizeof(Template) * r.tmpl.size(), cudaMemcpyHostToDevice, st));
+  uint8_t ar[kMaxLabels] = {};
+  for (size_t i = 0; i < r.arity.size() && i < kMaxLabels; i++) ar[i] = (uint8_t)r.arity[i];
+  FX(cudaMemcpyAsync(fx + kFxArity, ar, sizeof ar, cudaMemcpyHostToDevice, st));
+  if (!nr.pairs.empty())
+    FX(cudaMemcpyAsync(fx + kFxFront0, nr.pairs.data(), sizeof(Pair) * nr.pairs.size(), cudaMemcpyHostToDevice, st));
+  const unsigned long long ctr0 = (unsigned long long)nr.pairs.size() << kNetPairShift;
+  FX(cudaMemcpyAsync(fx + kFxNetctr + sizeof(unsigned long long) * (size_t)net_id, &ctr0, sizeof ctr0,
+                     cudaMemcpyHostToDevice, st));
+  Ctrl hc;
+  memset(&hc, 0, sizeof hc);
+  hc.stop_step = 0xFFFFFFFFu;
+  hc.fcount[0] = (uint32_t)nr.pairs.size();
+  hc.a_bump = ctx->st_nodes.size();
+  hc.v_bump = ctx->st_vars.size();
+  hc.live = (long long)ctx->st_nodes.size();
+  FX(cudaMemcpyAsync(fx + kFxCtrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+  Dev d;
+  memset(&d, 0, sizeof d);
+  d.node = nodes;
+  d.var = vars;
+  d.front[0] = reinterpret_cast<Pair*>(fx + kFxFront0);
+  d.front[1] = reinterpret_cast<Pair*>(fx + kFxFront1);
+  d.afree = reinterpret_cast<uint32_t*>(fx + kFxAfree);
+  d.vfree = reinterpret_cast<uint32_t*>(fx + kFxVfree);
+  d.netctr = reinterpret_cast<unsigned long long*>(fx + kFxNetctr);
+  d.netstat = reinterpret_cast<int32_t*>(fx + kFxNetstat);
+  d.rule_hist = reinterpret_cast<unsigned long long*>(fx + kFxHist);
+  d.ctrl = reinterpret_cast<Ctrl*>(fx + kFxCtrl);
+  d.table = reinterpret_cast<const int16_t*>(fx + kFxTable);
+  d.tmpl = reinterpret_cast<const Template*>(fx + kFxTmpl);
+  d.arity = reinterpret_cast<const uint8_t*>(fx + kFxArity);
+  d.trace_front = nullptr;
+  d.trace_live = nullptr;
+  d.trace_cap = 0;
+  d.cap_agents = max_agents;
+  d.cap_vars = max_vars;
+  d.cap_pairs = kFixedPairs;
+  d.max_nets = kFixedNets;
+  d.n_labels = (uint32_t)r.n_labels();
+  d.n_tmpl = (uint32_t)r.tmpl.size();
+  d.timeout_ns = kDefaultTimeoutNs;
+  d.slice_ns = kSliceNs;
+  const int B = 256;
+  d.solo_max = B;
+  const size_t smem = smem_bytes(B, d.n_labels, d.n_tmpl);
+  int nsm = 0, per = 0;
+  FX(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+  FX(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FX(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem));
+  const int grid = std::max(1, per) * nsm;
+  if (!nr.pairs.empty()) {
+    for (;;) {
+      void* args[] = {&d};
+      FX(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3((unsigned)B), args, smem, st));
+      uint32_t hit = 0;
+      FX(cudaMemcpyAsync(&hit, &d.ctrl->hit_slice, 4, cudaMemcpyDeviceToHost, st));
+      FX(cudaStreamSynchronize(st));
+      if (!hit) break;
+      const unsigned long long zero = 0;
+      FX(cudaMemcpyAsync(&d.ctrl->done, &zero, 4, cudaMemcpyHostToDevice, st));
+      FX(cudaMemcpyAsync(&d.ctrl->hit_slice, &zero, 4, cudaMemcpyHostToDevice, st));
+      FX(cudaMemcpyAsync(&d.ctrl->slice_t0, &zero, 8, cudaMemcpyHostToDevice, st));
+    }
+  }
+  int32_t err[2] = {0, 0};
+  FX(cudaMemcpyAsync(&err[0], &d.ctrl->error, 4, cudaMemcpyDeviceToHost, st));
+  FX(cudaMemcpyAsync(&err[1], &d.ctrl->fatal, 4, cudaMemcpyDeviceToHost, st));
+  unsigned long long ctr = 0;
+  FX(cudaMemcpyAsync(&ctr, d.netctr + net_id, sizeof ctr, cudaMemcpyDeviceToHost, st));
+  auto si = r.index.find("S");
+  auto zi = r.index.find("Z");
+  long long nat = -1;
+  if (nr.iface.size() == 1 && si != r.index.end() && zi != r.index.end()) {
+    long long* out = reinterpret_cast<long long*>(fx + kFxOut);
+    k_fixed_read_nat<<<1, 1, 0, st>>>(nodes, vars, max_agents, max_vars, nr.iface[0], si->second, zi->second, out);
+    FX(cudaGetLastError());
+    FX(cudaMemcpyAsync(&nat, out, sizeof nat, cudaMemcpyDeviceToHost, st));
+  }
+  FX(cudaStreamSynchronize(st));
+#undef FX
+  if (interactions_out) *interactions_out = ctr & kNetIntMask;
+  if (err[1]) return fail(ctx, err[1], "the reduction hit a capacity or state error");
+  if (err[0]) return fail(ctx, err[0], "active pair without a rule");
+  if (nat < 0) return fail(ctx, INET_ERR_INVALID_ARG, "the interface is not a numeral S^k(Z)");
+  *value_out = (uint64_t)nat;
+  return INET_OK;
+}
