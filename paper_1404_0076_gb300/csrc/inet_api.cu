@@ -25,6 +25,8 @@ constexpr uint64_t kDefaultPairs = 1ull << 21;
 constexpr uint32_t kDefaultNets = 1u << 16;
 constexpr unsigned long long kDefaultTimeoutNs = 10ull * 1000 * 1000 * 1000;
 constexpr unsigned long long kSliceNs = 2ull * 1000 * 1000 * 1000;
+constexpr uint32_t kMaxSolo = 1024;
+constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Layout {
   size_t ctrl, node, var, front0, front1, afree, vfree, netctr, netstat, hist, table, tmpl, arity,
@@ -597,9 +599,15 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   CK(cudaMemsetAsync(ctx->dev.rule_hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
   Dev d = ctx->dev;
   d.timeout_ns = o.timeout_ns ? o.timeout_ns : kDefaultTimeoutNs;
-  const size_t smem = smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl);
+  // persistent kernel: frontiers of at most solo_max pairs run on block 0
+  // with the frontier in shared memory (8 slots per pair, two buffers)
+  d.solo_max = o.solo_max < 0 ? 0u : (o.solo_max == 0 ? (uint32_t)B : (uint32_t)o.solo_max);
+  if (d.solo_max > kMaxSolo) return fail(ctx, INET_ERR_INVALID_ARG, "solo_max may not exceed 1024");
+  const size_t smem = smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl, 0);
+  const size_t smem_p = smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl, d.solo_max);
+  if (smem_p > kMaxSmem) return fail(ctx, INET_ERR_INVALID_ARG, "block size and solo_max need too much shared memory");
   CK(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CK(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   uint64_t launches = 0;
   if (fc[cur] > 0) {
@@ -635,10 +643,14 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
         if (s) return s;
       } else {
         int per = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem_p));
         const int maxg = std::max(1, per) * ctx->num_sms;
         grid = grid > 0 ? std::min(grid, maxg) : maxg;
-        d.solo_max = o.solo_max < 0 ? 0u : (o.solo_max == 0 ? (uint32_t)B : (uint32_t)o.solo_max);
+        // the step word the blocks start from
+        const unsigned long long word = pack_word(fc[cur], 0, cur, 0);
+        static const uint32_t zero4 = 0;
+        CK(h2d(ctx, &ctx->dev.ctrl->bar_word, &word, 8));
+        CK(h2d(ctx, &ctx->dev.ctrl->bar_count, &zero4, 4));
       }
       for (;;) {
         if (o.mode == INET_MODE_GRAPH) {
@@ -646,7 +658,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
         } else {
           void* args[] = {&d};
           CK(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3((unsigned)B), args,
-                                         smem, ctx->stream));
+                                         smem_p, ctx->stream));
         }
         launches++;
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -658,6 +670,15 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
         CK(h2d(ctx, &ctx->dev.ctrl->done, &zero8, 4));
         CK(h2d(ctx, &ctx->dev.ctrl->hit_slice, &zero8, 4));
         CK(h2d(ctx, &ctx->dev.ctrl->slice_t0, &zero8, 8));
+        if (o.mode == INET_MODE_PERSISTENT) {
+          uint32_t stp = 0, fcn[2] = {0, 0};
+          CK(d2h(ctx, &stp, &ctx->dev.ctrl->step, 4));
+          CK(d2h(ctx, fcn, ctx->dev.ctrl->fcount, 8));
+          CK(cudaStreamSynchronize(ctx->stream));
+          const unsigned long long word = pack_word(fcn[stp & 1u], 0, stp & 1u, 0);
+          CK(h2d(ctx, &ctx->dev.ctrl->bar_word, &word, 8));
+          CK(h2d(ctx, &ctx->dev.ctrl->bar_count, &zero8, 4));
+        }
       }
     }
   }
@@ -1026,13 +1047,15 @@ extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void
   d.slice_ns = kSliceNs;
   const int B = 256;
   d.solo_max = B;
-  const size_t smem = smem_bytes(B, d.n_labels, d.n_tmpl);
+  const size_t smem = smem_bytes(B, d.n_labels, d.n_tmpl, d.solo_max);
   int nsm = 0, per = 0;
   FX(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
   FX(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FX(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem));
   const int grid = std::max(1, per) * nsm;
   if (!nr.pairs.empty()) {
+    const unsigned long long word0 = pack_word((uint32_t)nr.pairs.size(), 0, 0, 0);
+    FX(cudaMemcpyAsync(&d.ctrl->bar_word, &word0, 8, cudaMemcpyHostToDevice, st));
     for (;;) {
       void* args[] = {&d};
       FX(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3((unsigned)B), args, smem, st));
@@ -1044,6 +1067,13 @@ extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void
       FX(cudaMemcpyAsync(&d.ctrl->done, &zero, 4, cudaMemcpyHostToDevice, st));
       FX(cudaMemcpyAsync(&d.ctrl->hit_slice, &zero, 4, cudaMemcpyHostToDevice, st));
       FX(cudaMemcpyAsync(&d.ctrl->slice_t0, &zero, 8, cudaMemcpyHostToDevice, st));
+      uint32_t stp = 0, fcn[2] = {0, 0};
+      FX(cudaMemcpyAsync(&stp, &d.ctrl->step, 4, cudaMemcpyDeviceToHost, st));
+      FX(cudaMemcpyAsync(fcn, d.ctrl->fcount, 8, cudaMemcpyDeviceToHost, st));
+      FX(cudaStreamSynchronize(st));
+      const unsigned long long word = pack_word(fcn[stp & 1u], 0, stp & 1u, 0);
+      FX(cudaMemcpyAsync(&d.ctrl->bar_word, &word, 8, cudaMemcpyHostToDevice, st));
+      FX(cudaMemcpyAsync(&d.ctrl->bar_count, &zero, 4, cudaMemcpyHostToDevice, st));
     }
   }
   int32_t err[2] = {0, 0};

@@ -125,7 +125,7 @@ def test_several_tiles_and_ragged_tail(orc, mode, block):
     assert tr[0] == summed_rounds(o)
 
 
-@pytest.mark.parametrize("solo_max", [-1, 64, 100000])
+@pytest.mark.parametrize("solo_max", [-1, 64, 1024])
 def test_persistent_solo_and_wide(orc, solo_max):
     nets = [W.fib_net(14), W.ack_net(3, 2), W.mul_net(8, 8)] + [W.add_net(i, 3) for i in range(300)]
     o = orc.run(R, nets, mode="rounds")
