@@ -71,21 +71,28 @@ enum {
                                device-to-host read of the frontier size per step */
   INET_MODE_GRAPH = 1,      /* the step kernel inside a CUDA graph with a
                                conditional WHILE node; no host round trip */
-  INET_MODE_PERSISTENT = 2  /* one cooperative launch; a grid barrier between
+  INET_MODE_PERSISTENT = 2, /* one cooperative launch; a grid barrier between
                                steps; narrow frontiers run on one block */
+  INET_MODE_ASYNC = 3       /* one cooperative launch without steps: every warp
+                               reduces pairs as they appear (active pairs are
+                               independent, Sec. 2.1); no per-step trace */
 };
 
 typedef struct inet_reduce_opts {
   int32_t mode;          /* INET_MODE_* */
-  int32_t block;         /* threads per block, multiple of 32 in [64, 1024]; 0 = 256 */
-  int32_t grid;          /* blocks for GRAPH / PERSISTENT; 0 = automatic */
+  int32_t block;         /* threads per block, multiple of 32 in [64, 512] (ASYNC: [32, 256]); 0 = 256 */
+  int32_t grid;          /* blocks for GRAPH / PERSISTENT / ASYNC; 0 = automatic
+                            (ASYNC: one block per SM) */
   int32_t solo_max;      /* PERSISTENT: frontier sizes <= solo_max run on block 0
                             alone; 0 = automatic, < 0 = never */
   uint64_t max_steps;    /* stop after this many steps of this call (0 = no limit);
                             returns INET_ERR_STEP_LIMIT, state stays resumable */
   uint64_t timeout_ns;   /* limit of any device-side wait (0 = 10 s) */
-  int32_t trace;         /* 1 = record frontier size and live agents per step */
-  int32_t reserved;
+  int32_t trace;         /* 1 = record frontier size and live agents per step
+                            (not in ASYNC mode, which has no steps) */
+  int32_t slice_us;      /* ASYNC: if > 0 the call returns after about this many
+                            microseconds with INET_ERR_STEP_LIMIT when pairs are
+                            left (resumable); 0 = run to the end */
 } inet_reduce_opts;
 
 #define INET_MAX_RULES 64
@@ -237,7 +244,7 @@ inet_status inet_reset(inet_ctx* ctx);
  * On success *value_out is k when the net's interface is the numeral S^k(Z)
  * (otherwise INET_ERR_INVALID_ARG) and *interactions_out (may be NULL) the
  * number of interactions. */
-#define INET_FIXED_SCRATCH_BYTES 12647168u
+#define INET_FIXED_SCRATCH_BYTES 12647680u
 inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void* arena, size_t arena_bytes,
                              uint64_t max_agents, uint64_t max_vars, int device, void* stream,
                              uint64_t* value_out, uint64_t* interactions_out);

@@ -12,7 +12,7 @@ import importlib
 # The CUDA library is loaded on first use of `capi` (or anything that needs
 # it), so `paper_1404_0076_gb300.build` can be imported before it exists;
 # using the evaluator without the library raises ImportError.
-MODES = {"plain": 0, "graph": 1, "persistent": 2}
+MODES = {"plain": 0, "graph": 1, "persistent": 2, "async": 3}
 
 
 def __getattr__(name):
@@ -91,9 +91,10 @@ class Evaluator:
         return [capi_lazy.inet_load_net(self.ctx, t) for t in texts]
 
     def reduce(self, net_ids, mode: str = "persistent", block: int = 0, grid: int = 0, solo_max: int = 0,
-               max_steps: int = 0, timeout_s: float = 0.0, trace: bool = False, check: bool = True) -> dict:
+               max_steps: int = 0, timeout_s: float = 0.0, trace: bool = False, check: bool = True,
+               slice_us: int = 0) -> dict:
         o = capi_lazy.inet_reduce_opts(MODES[mode], block, grid, solo_max, max_steps, int(timeout_s * 1e9),
-                                  1 if trace else 0, 0)
+                                       1 if trace else 0, slice_us)
         rc, st = capi_lazy.inet_reduce(self.ctx, list(net_ids), o, check=check)
         return {"status": capi_lazy.STATUS_NAMES.get(rc, rc), "interactions": st.interactions, "steps": st.steps,
                 "max_frontier": st.max_frontier, "live_agents": st.live_agents,

@@ -33,6 +33,7 @@ STATUS_NAMES = {
 INET_MODE_PLAIN = 0
 INET_MODE_GRAPH = 1
 INET_MODE_PERSISTENT = 2
+INET_MODE_ASYNC = 3
 INET_MAX_RULES = 64
 
 EXPORTED = [
@@ -51,7 +52,7 @@ class inet_arena_cfg(C.Structure):
 class inet_reduce_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("block", C.c_int32), ("grid", C.c_int32), ("solo_max", C.c_int32),
                 ("max_steps", C.c_uint64), ("timeout_ns", C.c_uint64), ("trace", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("slice_us", C.c_int32)]
 
 
 class inet_reduce_stats(C.Structure):

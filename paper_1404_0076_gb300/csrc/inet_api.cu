@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "inet.h"
+#include "inet_async.cuh"
 #include "inet_kernels.cuh"
 #include "inet_text.h"
 
@@ -340,7 +341,7 @@ inet_status ensure_snapshot(inet_ctx* ctx) {
   // free agent slots: ring entries [a_head, a_tail)
   std::vector<uint8_t> is_free(ctx->a_bump, 0);
   const uint64_t cap = ctx->cfg.max_agents;
-  uint64_t nfree = hc.a_tail - hc.a_head;
+  uint64_t nfree = hc.a_tail > hc.a_head ? std::min<uint64_t>(hc.a_tail - hc.a_head, cap) : 0;
   if (nfree) {
     std::vector<uint32_t> ring(nfree);
     uint64_t h = hc.a_head % cap;
@@ -570,8 +571,13 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   memset(&o, 0, sizeof o);
   if (opts) o = *opts;
   const int B = o.block ? o.block : 256;
-  if (B < 64 || B > 512 || B % 32) return fail(ctx, INET_ERR_INVALID_ARG, "block must be a multiple of 32 in [64, 512]");
-  if (o.mode < INET_MODE_PLAIN || o.mode > INET_MODE_PERSISTENT) return fail(ctx, INET_ERR_INVALID_ARG, "bad mode");
+  if (o.mode < INET_MODE_PLAIN || o.mode > INET_MODE_ASYNC) return fail(ctx, INET_ERR_INVALID_ARG, "bad mode");
+  if (o.mode == INET_MODE_ASYNC) {
+    if (B < 32 || B > 256 || B % 32) return fail(ctx, INET_ERR_INVALID_ARG, "ASYNC block must be a multiple of 32 in [32, 256]");
+    if (o.max_steps) return fail(ctx, INET_ERR_INVALID_ARG, "ASYNC has no steps; bound a call with slice_us");
+  } else if (B < 64 || B > 512 || B % 32) {
+    return fail(ctx, INET_ERR_INVALID_ARG, "block must be a multiple of 32 in [64, 512]");
+  }
   DeviceGuard g(ctx->device);
   inet_status s = stage_nets(ctx, net_ids, n);
   if (s) return s;
@@ -610,7 +616,40 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   CK(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   uint64_t launches = 0;
-  if (fc[cur] > 0) {
+  bool async_paused = false;
+  if (fc[cur] > 0 && o.mode == INET_MODE_ASYNC) {
+    const size_t smem_a = async_smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl);
+    CK(cudaFuncSetAttribute(k_async, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+    int per = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async, B, smem_a));
+    const int maxg = std::max(1, per) * ctx->num_sms;
+    // default: one block per SM (more warps mostly add idle polling)
+    const int grid = o.grid > 0 ? std::min(o.grid, maxg) : std::min(maxg, ctx->num_sms);
+    if (o.slice_us > 0) d.slice_ns = (unsigned long long)o.slice_us * 1000ull;
+    uint32_t q = cur;
+    for (;;) {
+      d.qcur = q;
+      const uint32_t fill_blocks = (uint32_t)std::min<uint64_t>(65535, (ctx->cfg.max_pairs + 255) / 256);
+      k_async_fill<<<fill_blocks, 256, 0, ctx->stream>>>(d);
+      k_async_prep<<<1, 1, 0, ctx->stream>>>(d);
+      void* args[] = {&d};
+      CK(cudaLaunchCooperativeKernel((const void*)k_async, dim3((unsigned)grid), dim3((unsigned)B), args, smem_a,
+                                     ctx->stream));
+      k_async_post<<<1, 1, 0, ctx->stream>>>(d);
+      CK(cudaGetLastError());
+      launches += 4;
+      CK(cudaEventRecord(ctx->ev1, ctx->stream));
+      uint32_t st[10];  // step, done, error, error_info, stop_step, hit_limit, trace_on, call_step0, fatal, hit_slice
+      CK(d2h(ctx, st, ctx->dev.ctrl, sizeof st));
+      CK(cudaStreamSynchronize(ctx->stream));
+      q ^= 1u;
+      if (st[1]) break;
+      if (o.slice_us > 0) {
+        async_paused = true;
+        break;
+      }
+    }
+  } else if (fc[cur] > 0) {
     if (o.mode == INET_MODE_PLAIN) {
       // one launch and one 16-byte read of the frontier size per step
       uint32_t pending = fc[cur];
@@ -746,7 +785,8 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   }
   if (hc.error == INET_ERR_NO_RULE)
     return fail(ctx, INET_ERR_NO_RULE, "active pair without a rule in net " + std::to_string(hc.error_info));
-  if (hc.hit_limit) return fail(ctx, INET_ERR_STEP_LIMIT, "step limit reached; call inet_reduce again to continue");
+  if (hc.hit_limit || async_paused)
+    return fail(ctx, INET_ERR_STEP_LIMIT, "step limit reached; call inet_reduce again to continue");
   return INET_OK;
 }
 

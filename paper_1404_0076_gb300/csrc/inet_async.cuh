@@ -1,0 +1,731 @@
+// Asynchronous driver of the reduction loop: the same interaction (Sec. 2.2,
+// ->int), allocation and linking (->com) as the step kernels, but without
+// steps.  Active pairs are independent (Sec. 2.1: reducing one cannot
+// affect another), so nothing forces all pairs of a "loop iteration" to
+// finish before the next begins: every warp of one cooperative launch loops
+// on its own, each lane holding at most one active pair.  An interaction
+// that creates active pairs keeps the first as the lane's next pair, so a
+// sequential chain of interactions never leaves its lane; further pairs go
+// to a FIFO of tickets that idle lanes claim.  The loop ends when no active
+// pair is left anywhere (the count of pairs in flight reaches zero), as in
+// Sec. 3.6; a time slice or an error instead drains every pair back to a
+// frontier buffer so that the host can resume.
+//
+// Ordering without barriers: a lane writes its new agent records, then
+// publishes references to them only through release operations (the
+// acq_rel exchange on a name slot, the release store of a queue slot);
+// every lane that learns of an agent does so through the matching acquire,
+// so the records it then loads are the ones written.
+#pragma once
+
+#include "inet_kernels.cuh"
+
+namespace inet {
+
+constexpr int kAStack = 128;   // per-warp stack of free agent slots
+constexpr int kVStack = 128;   // per-warp stack of free name slots
+constexpr int kVStageW = 64;   // names freed while linking, per warp
+constexpr int kRefill = 32;    // slots fetched for the warp's stack when it runs dry
+constexpr unsigned long long kQEmpty = ~0ull;
+constexpr unsigned long long kNoTicket = ~0ull;
+
+struct WarpMem {
+  uint32_t vals[kNumVals][32];
+  Pair out[kMaxLink][32];
+  Pair xl[(kMaxLink - 1) * 32];  // extra pairs of one iteration, in lane order
+  uint32_t astk[kAStack];
+  uint32_t vstk[kVStack];
+  uint32_t vstage[kVStageW];
+  unsigned long long bc[10];  // lane-0 broadcasts
+  int acount, vcount, vstage_n, pad;
+};
+
+__host__ __device__ inline size_t async_smem_bytes(uint32_t block, uint32_t n_labels, uint32_t n_tmpl) {
+  size_t b = 0;
+  auto take = [&](size_t n, size_t align) { b = (b + align - 1) / align * align; b += n; };
+  take(sizeof(Template) * (n_tmpl ? n_tmpl : 1), 16);
+  take(sizeof(WarpMem) * (block / 32), 16);
+  take(sizeof(uint32_t) * INET_MAX_RULES, 16);
+  take(sizeof(int16_t) * n_labels * n_labels, 16);
+  return b + 16;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Queue slot encoding: the pair with bit 31 of `a` = lap parity of the
+// ticket (ticket / capacity), so a waiter never takes a previous lap's pair.
+__device__ __forceinline__ bool q_ready(unsigned long long v, unsigned long long ticket, unsigned long long cap) {
+  if (v == kQEmpty) return false;
+  return (((uint32_t)v) >> 31) == (uint32_t)((ticket / cap) & 1ull);
+}
+
+// ->com for the asynchronous kernel (the chase after a second arrival):
+// link_eq with freed name slots staged per warp.  The lane has fenced its
+// new records before linking; a lane that receives a reference through an
+// exchange loads the referenced record only after the exchange returned
+// (address dependency), so it sees the record written before the fence.
+__device__ __forceinline__ bool link_async(const Dev& d, WarpMem& W, uint32_t t, uint32_t u, Pair* out) {
+  for (uint32_t guard = 0;; guard++) {
+    if (is_agent(t) && is_agent(u)) {
+      out->a = idx_of(t);
+      out->b = idx_of(u);
+      return true;
+    }
+    if (!is_var(t)) {
+      uint32_t w = t;
+      t = u;
+      u = w;
+    }
+    if (!is_var(t) || guard > (1u << 24) || idx_of(t) >= d.cap_vars) {
+      set_error(d.ctrl, INET_ERR_STATE, 1);
+      return false;
+    }
+    const uint32_t x = idx_of(t);
+    const uint32_t old = atomicExch(d.var + x, u);
+    if (old == kEmpty) return false;
+    __stcg(d.var + x, kEmpty);
+    const int pos = atomicAdd(&W.vstage_n, 1);
+    if (pos < kVStageW) {
+      W.vstage[pos] = x;
+    } else {
+      const unsigned long long tp = atomicAdd(&d.ctrl->v_tail, 1ull);
+      __stcg(d.vfree + tp % d.cap_vars, x);
+    }
+    t = old;
+  }
+}
+
+__device__ __forceinline__ unsigned long long warp_excl_scan64(unsigned long long v, unsigned long long* total) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += t;
+  }
+  *total = __shfl_sync(kFull, inc, 31);
+  return inc - v;
+}
+
+// One interaction per lane whose `valid` is set (warp-collective).  The new
+// active pairs are left in W.out[0..return)[lane]; a pair that cannot be
+// reduced (no rule, corrupt state) is dropped and returns 0.  Lane 0's
+// `live` collects the change of live agents.
+__device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int16_t* tab, uint32_t* hist,
+                                   WarpMem& W, bool valid, uint32_t a, uint32_t b, long long& live) {
+  const int lane = threadIdx.x & 31;
+  Ctrl* c = d.ctrl;
+  uint32_t net = 0, ti = 0;
+  int4 ra = make_int4(0, 0, 0, 0), rb = ra;
+  if (valid && (a >= d.cap_agents || b >= d.cap_agents)) {
+    set_error(c, INET_ERR_STATE, 2);
+    valid = false;
+  }
+  if (valid) {
+    ra = ld_node(d.node + a);
+    rb = ld_node(d.node + b);
+    const uint32_t la = (uint32_t)ra.x & 0xFFu, lb = (uint32_t)rb.x & 0xFFu;
+    int e = (la < d.n_labels && lb < d.n_labels) ? tab[la * d.n_labels + lb] : -1;
+    net = (uint32_t)ra.x >> 8;
+    if (net >= d.max_nets) {
+      set_error(c, INET_ERR_STATE, 3);
+      valid = false;
+    } else if (e < 0) {
+      valid = false;
+      atomicCAS(d.netstat + net, 0, INET_ERR_NO_RULE);
+      set_error(c, INET_ERR_NO_RULE, net);
+      atomicAdd(d.netctr + net, (unsigned long long)(-(1ll << kNetPairShift)));
+    } else {
+      if (e & 1) {
+        int4 t = ra; ra = rb; rb = t;
+        uint32_t u = a; a = b; b = u;
+      }
+      ti = (uint32_t)e >> 1;
+    }
+  }
+  const Template& T = tmpl[ti];
+  const uint32_t n_new = valid ? T.n_new : 0u;
+  const uint32_t n_fresh = valid ? T.n_fresh : 0u;
+  const uint32_t need_a = n_new > 2 ? n_new - 2 : 0u;
+  const uint32_t free_a = valid && n_new < 2 ? 2 - n_new : 0u;
+  unsigned long long tot;
+  const unsigned long long ex = warp_excl_scan64(
+      (unsigned long long)need_a | ((unsigned long long)n_fresh << 16) | ((unsigned long long)free_a << 32), &tot);
+  if (lane == 0) {
+    const uint32_t Ka = (uint32_t)(tot & 0xFFFF), Kv = (uint32_t)((tot >> 16) & 0xFFFF);
+    const uint32_t Fa = (uint32_t)((tot >> 32) & 0xFFFF);
+    bool ok = true;
+    unsigned long long rb0, bb0;
+    uint32_t av0;
+    // agents: the warp's stack first; when it runs dry, one global pop
+    // serves this interaction and refills the stack with kRefill slots
+    int ac = W.acount;
+    const uint32_t ta = min((uint32_t)ac, Ka);
+    ac -= (int)ta;
+    const uint32_t ga = Ka - ta, gra = ga ? (uint32_t)kRefill : 0u;
+    ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &rb0, &av0, &bb0) && ok;
+    W.bc[0] = rb0;
+    W.bc[1] = bb0;
+    const uint32_t keep = min((uint32_t)(kAStack - ac) - gra, Fa);
+    W.bc[2] = (unsigned long long)av0 | ((unsigned long long)ta << 20) | ((unsigned long long)ac << 40);
+    W.bc[3] = (unsigned long long)keep | ((Fa > keep ? atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep)) : 0ull) << 16);
+    W.bc[8] = (unsigned long long)ga | ((unsigned long long)gra << 16) | ((unsigned long long)(ac + (int)gra) << 32);
+    W.acount = ac + (int)gra + (int)keep;
+    int vc = W.vcount;
+    const uint32_t tv = min((uint32_t)vc, Kv);
+    vc -= (int)tv;
+    const uint32_t gv = Kv - tv, grv = gv ? (uint32_t)kRefill : 0u;
+    W.vcount = vc + (int)grv;
+    ok = pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &rb0, &av0, &bb0) && ok;
+    W.bc[4] = rb0;
+    W.bc[5] = bb0;
+    W.bc[6] = (unsigned long long)av0 | ((unsigned long long)tv << 20) | ((unsigned long long)vc << 40);
+    W.bc[9] = (unsigned long long)gv | ((unsigned long long)grv << 16);
+    W.bc[7] = ok ? 0ull : 1ull;
+    live += (long long)Ka - (long long)Fa;
+    if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
+    W.vstage_n = 0;
+  }
+  __syncwarp();
+  if (W.bc[7]) valid = false;
+  uint32_t n_link = 0;
+  if (valid) {
+    const uint32_t oa = (uint32_t)(ex & 0xFFFF), ov = (uint32_t)((ex >> 16) & 0xFFFF);
+    const unsigned long long b2 = W.bc[2], b6 = W.bc[6];
+    const uint32_t aavail = (uint32_t)(b2 & 0xFFFFF), ta = (uint32_t)((b2 >> 20) & 0xFFFFF), abase = (uint32_t)(b2 >> 40);
+    const uint32_t vavail = (uint32_t)(b6 & 0xFFFFF), tv = (uint32_t)((b6 >> 20) & 0xFFFFF), vbase = (uint32_t)(b6 >> 40);
+    W.vals[kValExt + 0][lane] = (uint32_t)ra.y;
+    W.vals[kValExt + 1][lane] = (uint32_t)ra.z;
+    W.vals[kValExt + 2][lane] = (uint32_t)ra.w;
+    W.vals[kValExt + 3][lane] = (uint32_t)rb.y;
+    W.vals[kValExt + 4][lane] = (uint32_t)rb.z;
+    W.vals[kValExt + 5][lane] = (uint32_t)rb.w;
+    bool in_range = true;
+#pragma unroll
+    for (int j = 0; j < kMaxNew; j++) {
+      if ((uint32_t)j < n_new) {
+        uint32_t sl;
+        if (j == 0) {
+          sl = a;
+        } else if (j == 1) {
+          sl = b;
+        } else {
+          const uint32_t k = oa + (uint32_t)j - 2;
+          if (k < ta) sl = W.astk[abase + k];
+          else sl = pool_slot(d.afree, d.cap_agents, W.bc[0], aavail, W.bc[1], k - ta);
+          if (sl >= d.cap_agents) in_range = false;
+        }
+        W.vals[kValNew + j][lane] = mk_agent(sl);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kMaxFresh; v++) {
+      if ((uint32_t)v < n_fresh) {
+        const uint32_t k = ov + (uint32_t)v;
+        uint32_t x;
+        if (k < tv) x = W.vstk[vbase + k];
+        else x = pool_slot(d.vfree, d.cap_vars, W.bc[4], vavail, W.bc[5], k - tv);
+        if (x >= d.cap_vars) in_range = false;
+        else __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's release
+        W.vals[kValFresh + v][lane] = mk_var(x);
+      }
+    }
+    if (!in_range) {
+      set_error(c, INET_ERR_STATE, 4);
+      valid = false;
+    }
+  }
+  if (valid) {
+    const int32_t head_net = (int32_t)(net << 8);
+#pragma unroll
+    for (int j = 0; j < kMaxNew; j++) {
+      if ((uint32_t)j < n_new) {
+        const uint8_t c0 = T.src[j][0], c1 = T.src[j][1], c2 = T.src[j][2];
+        int4 rec;
+        rec.x = head_net | (int32_t)T.lab[j];
+        rec.y = c0 == kValNone ? 0 : (int32_t)W.vals[c0][lane];
+        rec.z = c1 == kValNone ? 0 : (int32_t)W.vals[c1][lane];
+        rec.w = c2 == kValNone ? 0 : (int32_t)W.vals[c2][lane];
+        st_node(d.node + idx_of(W.vals[kValNew + j][lane]), rec);
+      }
+    }
+    n_link = T.n_link;
+  }
+  // a4: link.  One fence makes this lane's new records and fresh names
+  // visible before an exchange can publish a reference to them; the first
+  // exchange of each of the first kBatch equations is then issued back to
+  // back, and only second arrivals continue (rarely) with a chase.
+  constexpr int kBatch = 4;
+  uint32_t np = 0;
+  const uint32_t max_link = __reduce_max_sync(kFull, n_link);
+  if (max_link) {
+    if (valid) __threadfence();
+    uint32_t lt[kBatch], lu[kBatch], lo[kBatch];
+#pragma unroll
+    for (int k = 0; k < kBatch; k++) {
+      lt[k] = 0;
+      lu[k] = 0;
+      lo[k] = kEmpty;
+      if ((uint32_t)k < n_link) {
+        uint32_t t = W.vals[T.link[k][0]][lane], u = W.vals[T.link[k][1]][lane];
+        if (!(is_agent(t) && is_agent(u))) {
+          if (!is_var(t)) {
+            const uint32_t w = t;
+            t = u;
+            u = w;
+          }
+          if (is_var(t) && idx_of(t) < d.cap_vars) lo[k] = atomicExch(d.var + idx_of(t), u);
+          else set_error(c, INET_ERR_STATE, 1);
+        }
+        lt[k] = t;
+        lu[k] = u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kBatch; k++) {
+      if ((uint32_t)k < n_link) {
+        const uint32_t t = lt[k], u = lu[k];
+        if (is_agent(t) && is_agent(u)) {
+          W.out[np][lane] = Pair{idx_of(t), idx_of(u)};
+          np++;
+        } else if (lo[k] != kEmpty && is_var(t)) {
+          // second arrival: the slot is finished; continue with old = u
+          const uint32_t x = idx_of(t);
+          __stcg(d.var + x, kEmpty);
+          const int pos = atomicAdd(&W.vstage_n, 1);
+          if (pos < kVStageW) {
+            W.vstage[pos] = x;
+          } else {
+            const unsigned long long tp = atomicAdd(&c->v_tail, 1ull);
+            __stcg(d.vfree + tp % d.cap_vars, x);
+          }
+          Pair out;
+          if (link_async(d, W, lo[k], u, &out)) {
+            W.out[np][lane] = out;
+            np++;
+          }
+        }
+      }
+    }
+    for (uint32_t k = kBatch; k < max_link; k++) {
+      if (k < n_link) {
+        Pair out;
+        if (link_async(d, W, W.vals[T.link[k][0]][lane], W.vals[T.link[k][1]][lane], &out)) {
+          W.out[np][lane] = out;
+          np++;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // refills of the warp's stacks (after every taken entry has been read)
+  if (!W.bc[7]) {
+    const unsigned long long b8 = W.bc[8], b9 = W.bc[9];
+    const uint32_t ga = (uint32_t)(b8 & 0xFFFF), gra = (uint32_t)((b8 >> 16) & 0xFFFF);
+    const uint32_t abase = (uint32_t)(W.bc[2] >> 40), aavail = (uint32_t)(W.bc[2] & 0xFFFFF);
+    if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, W.bc[0], aavail, W.bc[1], ga + lane);
+    const uint32_t gv = (uint32_t)(b9 & 0xFFFF), grv = (uint32_t)((b9 >> 16) & 0xFFFF);
+    const uint32_t vbase = (uint32_t)(W.bc[6] >> 40), vavail = (uint32_t)(W.bc[6] & 0xFFFFF);
+    if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, W.bc[4], vavail, W.bc[5], gv + lane);
+  }
+  // agent frees: on the warp's stack above the refill, or the ring
+  if (valid && free_a) {
+    const uint32_t of = (uint32_t)((ex >> 32) & 0xFFFF);
+    const unsigned long long b3 = W.bc[3];
+    const uint32_t keep = (uint32_t)(b3 & 0xFFFF);
+    const unsigned long long over = b3 >> 16;
+    const uint32_t abase = (uint32_t)(W.bc[8] >> 32);
+    for (uint32_t f = 0; f < free_a; f++) {
+      const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
+      const uint32_t k = of + f;
+      if (k < keep) W.astk[abase + k] = slot;
+      else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
+    }
+  }
+  // freed names: on the warp's stack, the overflow to the ring
+  {
+    const int nv = min(W.vstage_n, kVStageW);
+    const int vc = W.vcount;
+    const int keep = min(kVStack - vc, nv);
+    unsigned long long over = 0;
+    if (lane == 0 && nv > keep) over = atomicAdd(&c->v_tail, (unsigned long long)(nv - keep));
+    over = __shfl_sync(kFull, over, 0);
+    for (int j = lane; j < nv; j += 32) {
+      if (j < keep) W.vstk[vc + j] = W.vstage[j];
+      else __stcg(d.vfree + (over + (unsigned long long)(j - keep)) % d.cap_vars, W.vstage[j]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      W.vcount = vc + keep;
+      W.vstage_n = 0;
+    }
+    __syncwarp();
+  }
+  // per-net counters and the rule histogram
+  const unsigned vm = __ballot_sync(kFull, valid);
+  if (valid) {
+    const unsigned peers = __match_any_sync(vm, net);
+    if (peers == vm) {
+      const uint32_t tp = __reduce_add_sync(vm, np);
+      const uint32_t cnt = __popc(vm);
+      if (lane == __ffs(vm) - 1)
+        atomicAdd(d.netctr + net, (unsigned long long)cnt +
+                                      ((unsigned long long)((long long)tp - (long long)cnt) << kNetPairShift));
+    } else {
+      atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)np - 1) << kNetPairShift));
+    }
+    const unsigned rp = __match_any_sync(vm, (unsigned)T.rule);
+    if (lane == __ffs(rp) - 1) atomicAdd(&hist[T.rule], (uint32_t)__popc(rp));
+  }
+  return valid ? np : 0u;
+}
+
+// Writes a pair back to the exit frontier (other buffer).
+__device__ __forceinline__ void exit_pair(const Dev& d, Pair p) {
+  const uint32_t k = atomicAdd(&d.ctrl->aexit, 1u);
+  if (k < d.cap_pairs) {
+    __stcg(reinterpret_cast<unsigned long long*>(d.front[d.qcur ^ 1u] + k), *reinterpret_cast<unsigned long long*>(&p));
+  } else {
+    set_error(d.ctrl, INET_ERR_ARENA_FULL, 5);
+  }
+}
+
+// Bounded wait for a ticket's slot; returns false on timeout.
+__device__ __forceinline__ bool wait_slot(const Dev& d, const unsigned long long* slot, unsigned long long ticket,
+                                          unsigned long long cap, unsigned long long* v) {
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t spin = 0;; spin++) {
+    *v = ld_acquire64(slot);
+    if (q_ready(*v, ticket, cap)) return true;
+    __nanosleep(64);
+    if ((spin & 63) == 63 && globaltimer() - t0 > d.timeout_ns) {
+      set_error(d.ctrl, INET_ERR_TIMEOUT, 6);
+      return false;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_async(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  size_t off = 0;
+  auto take = [&](size_t n) { off = (off + 15) / 16 * 16; unsigned char* p = smem_raw + off; off += n; return p; };
+  Template* tmpl = reinterpret_cast<Template*>(take(sizeof(Template) * (d.n_tmpl ? d.n_tmpl : 1)));
+  WarpMem* wm = reinterpret_cast<WarpMem*>(take(sizeof(WarpMem) * (blockDim.x / 32)));
+  uint32_t* hist = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * INET_MAX_RULES));
+  int16_t* tab = reinterpret_cast<int16_t*>(take(sizeof(int16_t) * d.n_labels * d.n_labels));
+  const uint32_t nt = d.n_tmpl * (sizeof(Template) / 16);
+  for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x)
+    reinterpret_cast<int4*>(tmpl)[i] = reinterpret_cast<const int4*>(d.tmpl)[i];
+  for (uint32_t i = threadIdx.x; i < d.n_labels * d.n_labels; i += blockDim.x) tab[i] = d.table[i];
+  for (uint32_t i = threadIdx.x; i < INET_MAX_RULES; i += blockDim.x) hist[i] = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpMem& W = wm[wid];
+  if (lane == 0) {
+    W.acount = 0;
+    W.vcount = 0;
+    W.vstage_n = 0;
+  }
+  __syncthreads();
+  Ctrl* c = d.ctrl;
+  Pair* Q = d.front[d.qcur];
+  const unsigned long long cap = d.cap_pairs;
+  const uint32_t total_warps = gridDim.x * (blockDim.x / 32);
+  bool have = false;
+  uint32_t pa = 0, pb = 0;
+  unsigned long long ticket = kNoTicket, tslot = 0;
+  uint32_t tlap = 0;
+  long long live = 0;
+  uint32_t nap = 0;
+  bool stop = false, finished = false;
+  unsigned long long t_start = 0;
+  if (lane == 0) {
+    const unsigned long long now = globaltimer();
+    atomicCAS(&c->slice_t0, 0ull, now);
+    t_start = ld_volatile64(&c->slice_t0);
+  }
+  for (uint32_t it = 0;; it++) {
+    // stop / slice checks every 16 iterations
+    if ((it & 15) == 15) {
+      uint32_t st = 0;
+      if (lane == 0) {
+        st = ld_volatile(&c->astop) | (ld_volatile((const uint32_t*)&c->fatal) ? 1u : 0u);
+        if (!st && globaltimer() - t_start > d.slice_ns) {
+          c->astop = 1;
+          c->hit_slice = 1;
+          st = 1;
+        }
+      }
+      if (__shfl_sync(kFull, st, 0)) {
+        stop = true;
+        break;
+      }
+    }
+    // claim tickets for lanes without work when the queue has unclaimed
+    // pairs (a warp that is busy anyway looks only every 8th iteration)
+    const unsigned want = __ballot_sync(kFull, !have && ticket == kNoTicket);
+    const unsigned busy = __ballot_sync(kFull, have);
+    if (want && (!busy || (it & 7) == 0)) {
+      unsigned long long base = 0;
+      uint32_t k = 0;
+      if (lane == 0) {
+        unsigned long long qh, qt;
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(qh), "=l"(qt) : "l"(&c->q_head) : "memory");
+        if (qt > qh) {
+          k = (uint32_t)min((unsigned long long)__popc(want), qt - qh);
+          base = atomicAdd(&c->q_head, (unsigned long long)k);
+        }
+      }
+      k = __shfl_sync(kFull, k, 0);
+      if (k) {
+        unsigned long long bm = 0, bl = 0;
+        if (lane == 0) {
+          bm = base % cap;
+          bl = (base / cap) & 1ull;
+        }
+        base = __shfl_sync(kFull, base, 0);
+        bm = __shfl_sync(kFull, bm, 0);
+        bl = __shfl_sync(kFull, bl, 0);
+        const unsigned rank = __popc(want & lanemask_lt());
+        if (((want >> lane) & 1u) && rank < k) {
+          ticket = base + rank;
+          tslot = bm + rank;
+          tlap = (uint32_t)bl;
+          if (tslot >= cap) {
+            tslot -= cap;
+            tlap ^= 1u;
+          }
+        }
+      }
+    }
+    // poll claimed tickets
+    if (!have && ticket != kNoTicket) {
+      unsigned long long* slot = reinterpret_cast<unsigned long long*>(Q + tslot);
+      const unsigned long long v = ld_acquire64(slot);
+      if (v != kQEmpty && (((uint32_t)v) >> 31) == tlap) {
+        *reinterpret_cast<volatile unsigned long long*>(slot) = kQEmpty;
+        pa = ((uint32_t)v) & 0x7FFFFFFFu;
+        pb = (uint32_t)(v >> 32);
+        have = true;
+        ticket = kNoTicket;
+      }
+    }
+    const unsigned act = __ballot_sync(kFull, have);
+    if (!act) {
+      // idle: the loop is over when no pair is left anywhere
+      uint32_t fin = 0;
+      if (lane == 0) fin = ld_volatile_s64(&c->inflight) == 0 ? 1u : 0u;
+      if (__shfl_sync(kFull, fin, 0)) {
+        finished = true;
+        break;
+      }
+      __nanosleep(nap);
+      nap = nap < 1024 ? nap * 2 + 32 : 1024;
+      continue;
+    }
+    nap = 0;
+    const uint32_t np = async_interact(d, tmpl, tab, hist, W, have, pa, pb, live);
+    // keep the first new pair; queue the rest
+    const bool had = have;
+    have = np > 0;
+    if (have) {
+      const Pair p0 = W.out[0][lane];
+      pa = p0.a;
+      pb = p0.b;
+    }
+    const uint32_t extra = np > 1 ? np - 1 : 0u;
+    // pairs in flight: each new pair beyond a lane's own next one joins
+    // before it is published (lane 0 waits until the increment is performed,
+    // so no consumer's decrement can overtake it); each pair that produced
+    // nothing leaves afterwards
+    long long grow = extra, shrink = had && np == 0 ? -1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      grow += __shfl_xor_sync(kFull, grow, o);
+      shrink += __shfl_xor_sync(kFull, shrink, o);
+    }
+    if (lane == 0 && grow) {
+      const unsigned long long r = atomicAdd(reinterpret_cast<unsigned long long*>(&c->inflight), (unsigned long long)grow);
+      asm volatile("" ::"l"(r));
+    }
+    __syncwarp();
+    {
+      // extra pairs go first to idle lanes of this warp (through shared
+      // memory), the rest to the ticket queue
+      unsigned inc = extra;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const unsigned totx = __shfl_sync(kFull, inc, 31);
+      if (totx) {
+        for (uint32_t j = 0; j < extra; j++) W.xl[inc - extra + j] = W.out[1 + j][lane];
+        const unsigned idle = __ballot_sync(kFull, !have && ticket == kNoTicket);
+        const unsigned nidle = __popc(idle);
+        __syncwarp();
+        const unsigned local = min(nidle, totx);
+        if ((idle >> lane) & 1u) {
+          const unsigned r = __popc(idle & lanemask_lt());
+          if (r < local) {
+            const Pair p = W.xl[r];
+            pa = p.a;
+            pb = p.b;
+            have = true;
+          }
+        }
+        const unsigned toq = totx - local;
+        if (toq) {
+          unsigned long long qm = 0, ql = 0;
+          if (lane == 0) {
+            const unsigned long long qb = atomicAdd(&c->q_tail, (unsigned long long)toq);
+            qm = qb % cap;
+            ql = (qb / cap) & 1ull;
+          }
+          qm = __shfl_sync(kFull, qm, 0);
+          ql = __shfl_sync(kFull, ql, 0);
+          for (unsigned j = lane; j < toq; j += 32) {
+            unsigned long long si = qm + j;
+            uint32_t lap = (uint32_t)ql;
+            if (si >= cap) {
+              si -= cap;
+              lap ^= 1u;
+            }
+            unsigned long long* slot = reinterpret_cast<unsigned long long*>(Q + si);
+            const unsigned long long t0 = globaltimer();
+            while (ld_volatile64(slot) != kQEmpty) {  // the previous lap's pair is not taken yet
+              __nanosleep(64);
+              if (globaltimer() - t0 > d.timeout_ns) {
+                set_error(c, INET_ERR_TIMEOUT, 7);
+                break;
+              }
+            }
+            const Pair p = W.xl[local + j];
+            st_release64(slot, (unsigned long long)(p.a | (lap << 31)) | ((unsigned long long)p.b << 32));
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (lane == 0 && shrink) atomicAdd(reinterpret_cast<unsigned long long*>(&c->inflight), (unsigned long long)shrink);
+    __syncwarp();
+  }
+  // leaving: publish live agents; a stop drains every pair to the other buffer
+  if (lane == 0 && live) atomicAdd(reinterpret_cast<unsigned long long*>(&c->live), (unsigned long long)live);
+  if (finished && !stop) {
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(&c->quiesce, 1u);
+    }
+  } else {
+    uint32_t ok = 1;
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(&c->quiesce, 1u);
+      const unsigned long long t0 = globaltimer();
+      while (ld_volatile(&c->quiesce) < total_warps) {
+        __nanosleep(256);
+        if (globaltimer() - t0 > d.timeout_ns) {
+          set_error(c, INET_ERR_TIMEOUT, 8);
+          ok = 0;
+          break;
+        }
+      }
+      __threadfence();
+    }
+    ok = __shfl_sync(kFull, ok, 0);
+    if (ok) {
+      const unsigned long long qt = ld_volatile64(&c->q_tail);
+      if (!have && ticket != kNoTicket && ticket < qt) {
+        unsigned long long v;
+        if (wait_slot(d, reinterpret_cast<unsigned long long*>(Q + ticket % cap), ticket, cap, &v)) {
+          pa = ((uint32_t)v) & 0x7FFFFFFFu;
+          pb = (uint32_t)(v >> 32);
+          have = true;
+        }
+      }
+      if (have) exit_pair(d, Pair{pa, pb});
+      // unclaimed tickets, shared among the warps
+      const unsigned long long qh = ld_volatile64(&c->q_head);
+      const uint32_t gw = blockIdx.x * (blockDim.x / 32) + (uint32_t)wid;
+      for (unsigned long long tk = qh + (unsigned long long)gw * 32 + lane; tk < qt;
+           tk += (unsigned long long)total_warps * 32) {
+        unsigned long long v;
+        if (wait_slot(d, reinterpret_cast<unsigned long long*>(Q + tk % cap), tk, cap, &v))
+          exit_pair(d, Pair{((uint32_t)v) & 0x7FFFFFFFu, (uint32_t)(v >> 32)});
+      }
+    }
+  }
+  // free slots known only to this warp go back to the rings
+  __syncwarp();
+  {
+    unsigned long long ab = 0, vb = 0;
+    if (lane == 0) {
+      if (W.acount) ab = atomicAdd(&c->a_tail, (unsigned long long)W.acount);
+      if (W.vcount) vb = atomicAdd(&c->v_tail, (unsigned long long)W.vcount);
+    }
+    ab = __shfl_sync(kFull, ab, 0);
+    vb = __shfl_sync(kFull, vb, 0);
+    for (int j = lane; j < W.acount; j += 32) __stcg(d.afree + (ab + j) % d.cap_agents, W.astk[j]);
+    for (int j = lane; j < W.vcount; j += 32) __stcg(d.vfree + (vb + j) % d.cap_vars, W.vstk[j]);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < d.n_tmpl; i += blockDim.x)
+    if (hist[i]) atomicAdd(&d.rule_hist[i], (unsigned long long)hist[i]);
+}
+
+// Before an asynchronous launch: mark every queue slot past the current
+// frontier empty.
+__global__ void k_async_fill(Dev d) {
+  const uint32_t n0 = min(d.ctrl->fcount[d.qcur], d.cap_pairs);
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(d.front[d.qcur]);
+  for (unsigned long long i = n0 + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < d.cap_pairs;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    q[i] = kQEmpty;
+}
+
+// Before an asynchronous launch (one thread): publish the rings, make the
+// current frontier the ticket queue.
+__global__ void k_async_prep(Dev d) {
+  Ctrl* c = d.ctrl;
+  const uint32_t n0 = min(c->fcount[d.qcur], d.cap_pairs);
+  if (c->a_head > c->a_pub) c->a_head = c->a_pub;
+  c->a_pub = c->a_tail;
+  if (c->v_head > c->v_pub) c->v_head = c->v_pub;
+  c->v_pub = c->v_tail;
+  c->q_head = 0;
+  c->q_tail = n0;
+  c->inflight = n0;
+  c->astop = 0;
+  c->quiesce = 0;
+  c->aexit = 0;
+  c->slice_t0 = 0;
+  c->hit_slice = 0;
+  c->done = 0;
+  __threadfence();
+}
+
+// After an asynchronous launch (one thread): the pairs written back become
+// the frontier of the other buffer.
+__global__ void k_async_post(Dev d) {
+  Ctrl* c = d.ctrl;
+  const uint32_t cur = d.qcur;
+  const uint32_t n = min(c->aexit, d.cap_pairs);
+  // pops that found the ring empty went to the bump pointer but advanced the head
+  if (c->a_head > c->a_pub) c->a_head = c->a_pub;
+  if (c->v_head > c->v_pub) c->v_head = c->v_pub;
+  c->fcount[cur] = 0;
+  c->fcount[cur ^ 1u] = n;
+  c->step = c->step + 1;
+  c->done = n == 0 || c->fatal != 0 ? 1u : 0u;
+  if (c->live > c->peak_live) c->peak_live = c->live;
+  __threadfence();
+}
+
+}  // namespace inet

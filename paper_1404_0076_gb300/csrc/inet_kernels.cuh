@@ -54,6 +54,13 @@ struct Ctrl {
   alignas(128) unsigned long long bar_word;
   alignas(128) uint32_t blocks_done;        // k_step: blocks finished this launch
   alignas(128) long long live;              // live agents, all nets
+  // asynchronous kernel: ticket queue, pairs in flight, stop/quiesce/exit
+  alignas(128) unsigned long long q_head;   // next ticket to claim (read together with q_tail)
+  unsigned long long q_tail;                // next ticket to fill
+  alignas(128) long long inflight;          // active pairs not yet reduced (queued or held)
+  alignas(128) uint32_t astop;              // 1: stop taking work, drain, exit
+  alignas(128) uint32_t quiesce;            // warps that stopped producing
+  alignas(128) uint32_t aexit;              // pairs written back to the other frontier buffer
 };
 
 // Published step word of the persistent kernel.
@@ -90,6 +97,8 @@ struct Dev {
   unsigned long long slice_ns;   // a launch stops at the first step boundary after this
   cudaGraphConditionalHandle cond;
   int use_cond;
+  uint32_t qcur;   // asynchronous kernel: frontier buffer used as the ticket queue
+  uint32_t pad2;
 };
 
 // ---------------------------------------------------------------------------
@@ -297,7 +306,7 @@ __device__ __forceinline__ bool pool_pop(unsigned long long* head, const unsigne
   const unsigned long long pub = ld_volatile64(pub_p);
   unsigned long long h = atomicAdd(head, (unsigned long long)k);
   uint32_t avail = h < pub ? (uint32_t)min((unsigned long long)k, pub - h) : 0u;
-  *ring_base = h;
+  *ring_base = h % cap;  // reduced once here; pool_slot adds k < cap without dividing
   *ring_avail = avail;
   if (avail < k) {
     unsigned long long need = k - avail;
@@ -311,7 +320,11 @@ __device__ __forceinline__ bool pool_pop(unsigned long long* head, const unsigne
 __device__ __forceinline__ uint32_t pool_slot(const uint32_t* ring, unsigned long long cap,
                                               unsigned long long ring_base, uint32_t ring_avail,
                                               unsigned long long bump_base, uint32_t k) {
-  if (k < ring_avail) return __ldcg(ring + (ring_base + k) % cap);
+  if (k < ring_avail) {
+    unsigned long long p = ring_base + k;  // ring_base < cap and k < cap
+    if (p >= cap) p -= cap;
+    return __ldcg(ring + p);
+  }
   return (uint32_t)(bump_base + (k - ring_avail));
 }
 
@@ -485,9 +498,9 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
           sl = b;
         } else {
           const uint32_t k = oa + (uint32_t)j - 2;
-          sl = k < ta ? s.la[la0 + k]
-                      : pool_slot(d.afree, d.cap_agents, s.warp[W_ARING], (uint32_t)s.warp[W_AAVAIL],
-                                  s.warp[W_ABUMP], k - ta);
+          if (k < ta) sl = s.la[la0 + k];
+          else sl = pool_slot(d.afree, d.cap_agents, s.warp[W_ARING], (uint32_t)s.warp[W_AAVAIL],
+                              s.warp[W_ABUMP], k - ta);
           if (sl >= d.cap_agents) in_range = false;
         }
         vals[(kValNew + j) * B] = mk_agent(sl);
@@ -497,9 +510,9 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
     for (int v = 0; v < kMaxFresh; v++) {
       if ((uint32_t)v < n_fresh) {
         const uint32_t k = ov + (uint32_t)v;
-        const uint32_t x = k < tv ? s.lv[lv0 + k]
-                                  : pool_slot(d.vfree, d.cap_vars, s.warp[W_VRING], (uint32_t)s.warp[W_VAVAIL],
-                                              s.warp[W_VBUMP], k - tv);
+        uint32_t x;
+        if (k < tv) x = s.lv[lv0 + k];
+        else x = pool_slot(d.vfree, d.cap_vars, s.warp[W_VRING], (uint32_t)s.warp[W_VAVAIL], s.warp[W_VBUMP], k - tv);
         if (x >= d.cap_vars) in_range = false;
         vals[(kValFresh + v) * B] = mk_var(x);
       }

@@ -242,3 +242,90 @@ def test_incremental_batches_share_the_loop(orc):
         assert ev.readback(i) == o[k]["result"]
         assert ev.net_info(i)["interactions"] == o[k]["interactions"]
     ev.close()
+
+
+# --- the asynchronous driver (no steps: results and counts, no per-step trace) ---
+
+@pytest.mark.parametrize("block", [32, 128, 256])
+def test_async_small_mixed_batch(orc, block):
+    o = orc.run(R, SMALL)
+    st, g, _ = run_gpu(R, SMALL, "async", block=block)
+    compare(o, g)
+    assert st["interactions"] == sum(x["interactions"] for x in o)
+    per_rule = [sum(x["per_rule"][r] for x in o) for r in range(len(o[0]["per_rule"]))]
+    assert st["per_rule"] == per_rule
+
+
+def test_async_many_nets_and_wide_fanout(orc):
+    nets = [W.add_net((7 * i) % 23, i % 5) for i in range(1000)] + [W.fib_net(14), W.mul_net(9, 8), W.ack_net(3, 3)]
+    o = orc.run(R, nets, quiet=True)
+    st, g, _ = run_gpu(R, nets, "async", text=False)
+    compare(o, g, text=False)
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+def test_async_full_size_configs(orc, cfg):
+    nets = full_config(cfg)
+    o = orc.run(R, nets, quiet=(cfg == 1), threads=os.cpu_count() or 4)
+    st, g, _ = run_gpu(R, nets, "async", text=(cfg != 1), max_agents=1 << 24, max_vars=1 << 24, max_pairs=1 << 21)
+    compare(o, g, text=(cfg != 1))
+    assert st["interactions"] == sum(x["interactions"] for x in o)
+
+
+def test_async_slices_are_resumable(orc):
+    nets = [W.fib_net(17), W.mul_net(12, 11)]
+    o = orc.run(R, nets)
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    st = ev.reduce(ids, mode="async", slice_us=200, check=False)
+    calls = 1
+    while st["status"] == "STEP_LIMIT":
+        st = ev.reduce([], mode="async", slice_us=200, check=False)
+        calls += 1
+        assert calls < 10000
+    assert st["status"] == "OK"
+    for k, i in enumerate(ids):
+        assert ev.readback(i) == o[k]["result"]
+        assert ev.net_info(i)["interactions"] == o[k]["interactions"]
+        assert ev.net_info(i)["live_agents"] == o[k]["live"]
+    ev.close()
+
+
+def test_async_then_steps_continue_the_same_nets(orc):
+    # a sliced asynchronous call leaves its pairs in the frontier, which the
+    # step kernels can finish (and the reverse)
+    nets = [W.fib_net(15), W.ack_net(2, 5)]
+    o = orc.run(R, nets)
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    ev.reduce(ids, mode="persistent", max_steps=30, check=False)
+    ev.reduce([], mode="async", slice_us=100, check=False)
+    ev.reduce([], mode="graph")
+    for k, i in enumerate(ids):
+        assert ev.readback(i) == o[k]["result"]
+        assert ev.net_info(i)["interactions"] == o[k]["interactions"]
+    ev.close()
+
+
+def test_async_no_rule_and_arena_full(orc):
+    rules = R + "Foo(x) = Bar -> x = Bar;\n"
+    nets = [W.add_net(5, 2), "< r | Foo(r) = Z >", W.fib_net(7)]
+    ev = make_ev()
+    ev.load_rules(rules)
+    ids = ev.load_nets(nets)
+    st = ev.reduce(ids, mode="async", check=False)
+    assert st["status"] == "NO_RULE"
+    o = orc.run(rules, [nets[0], nets[2]])
+    assert ev.readback(ids[0]) == o[0]["result"] and ev.readback(ids[2]) == o[1]["result"]
+    ev.close()
+    ev = make_ev(max_agents=400, max_vars=400, max_pairs=256)
+    ev.load_rules(R)
+    i = ev.load_net(W.fib_net(12))
+    assert ev.reduce([i], mode="async", check=False)["status"] == "ARENA_FULL"
+    ev.reset()
+    j = ev.load_net(W.add_net(4, 4))
+    ev.reduce([j], mode="async")
+    assert ev.readback_nat(j) == (8, 5)
+    ev.close()
