@@ -80,15 +80,18 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 
 
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
-# kernel source they were taken on (sha1 prefix of csrc/inet_kernels.cuh).
-NCU_TRAFFIC = {("mul2048", "persistent", "e16f5c9e0bc2"): 37_429_248 + 237_167_616}
+# kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
+# and csrc/inet_async.cuh).
+NCU_TRAFFIC = {("mul2048", "async", "84b80c5dae8d"): 10_279_168 + 16_092_160}
 
 
 def kernel_source_hash() -> str:
     import hashlib
-    p = os.path.join(ROOT, "paper_1404_0076_gb300", "csrc", "inet_kernels.cuh")
-    with open(p, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for name in ("inet_kernels.cuh", "inet_async.cuh"):
+        with open(os.path.join(ROOT, "paper_1404_0076_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def measured_peaks():
@@ -210,7 +213,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mul2048")
-    ap.add_argument("--mode", default="persistent", choices=["persistent", "graph", "plain"])
+    ap.add_argument("--mode", default="async", choices=["async", "persistent", "graph", "plain"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--solo-max", type=int, default=0)
@@ -277,14 +280,16 @@ def main():
         total_s_max, ints_all = total_s, float(ints)
     value = ints_all / total_s_max
 
-    # roofline of the dominant kernel (the persistent kernel: one launch per step)
+    # roofline of the dominant kernel: one launch of it per step (k_async or
+    # k_persistent) or, for the step kernels, per reduction step
     peak, peak_kind = measured_peaks()
-    launch_s = total_s / max(1, launches)
-    achieved = (alg_bytes / max(1, launches)) / launch_s / 1e9
+    achieved = alg_bytes / total_s / 1e9
     traffic = NCU_TRAFFIC.get((args.workload, args.mode, kernel_source_hash()))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "bytes_per_interaction": alg_bytes / max(1, ints),
-            "kernel": {"persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[args.mode]}
+            "kernel": {"async": "k_async", "persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[args.mode],
+            "launch_time": "device time of the reduce call (for async: the queue fill, set-up and wind-down "
+                           "kernels around k_async add a few microseconds)"}
 
     # e2e: public API from host text to host results, copies included
     e2e_ms, e2e_h2d, e2e_d2h, e2e_int = [], 0, 0, 0
@@ -305,9 +310,15 @@ def main():
            "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
            "ms_per_step": statistics.median(e2e_ms)}
 
-    # the plain host-driven loop: whole batch, and one net per launch sequence
+    # the other loop forms on the same batch (one run each), and the plain
+    # host-driven loop with one net per launch sequence
     plain = None
     if not args.no_plain and rank == 0:
+        forms = {}
+        for m in ("async", "persistent", "graph"):
+            prepared()
+            stm = ev.reduce([], mode=m)
+            forms[m] = stm["interactions"] / (stm["device_ms"] / 1e3)
         ids = prepared()
         stp = ev.reduce([], mode="plain")
         one = []
@@ -319,7 +330,7 @@ def main():
             torch.cuda.synchronize()
             s1 = ev.reduce([], mode="plain")
             one.append((s1["interactions"], s1["device_ms"]))
-        plain = {"batch_plain": stp["interactions"] / (stp["device_ms"] / 1e3),
+        plain = {"forms": forms, "batch_plain": stp["interactions"] / (stp["device_ms"] / 1e3),
                  "one_net_per_launch": sum(a for a, _ in one) / (sum(b for _, b in one) / 1e3),
                  "one_net_sample": f"first {len(sample)} nets, each reduced alone by the host-driven loop",
                  "unit": UNIT}
