@@ -60,7 +60,9 @@ enum {
 typedef struct inet_arena_cfg {
   uint64_t max_agents; /* agent slots, 16 bytes each (default 1<<22) */
   uint64_t max_vars;   /* name slots, 4 bytes each (default 1<<22) */
-  uint64_t max_pairs;  /* frontier capacity, 8 bytes per pair, two buffers (default 1<<21) */
+  uint64_t max_pairs;  /* frontier capacity: active pairs at once (default 1<<21); two
+                          buffers of 8 bytes per pair plus an 8-byte sequence number
+                          per cell of the asynchronous driver's ticket queue */
   uint32_t max_nets;   /* independent nets held at once (default 1<<16) */
   uint32_t reserved;
 } inet_arena_cfg;
@@ -75,7 +77,9 @@ enum {
                                steps; narrow frontiers run on one block */
   INET_MODE_ASYNC = 3       /* one cooperative launch without steps: every warp
                                reduces pairs as they appear (active pairs are
-                               independent, Sec. 2.1); no per-step trace */
+                               independent, Sec. 2.1); no per-step trace; more
+                               than max_pairs pairs in flight at once is
+                               INET_ERR_ARENA_FULL */
 };
 
 typedef struct inet_reduce_opts {
@@ -199,6 +203,19 @@ inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, 
  * INET_ERR_INVALID_ARG.  interactions_out (may be NULL) gets the net's
  * interaction count. */
 inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out, uint64_t* interactions_out);
+
+/* Pending active pairs of each listed net as of the end of the last
+ * inet_reduce() (0 = the net is in normal form).  Host-only: no device work,
+ * no copy. */
+inet_status inet_net_pending(const inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* pending_out);
+
+/* inet_readback_nat() for many nets at once, walked on the device (one
+ * thread per net, following name slots as ->col/->sub do, Theorem 1):
+ * values_out[i] = k when net i's interface is one numeral S^k(Z), else
+ * UINT64_MAX; interactions_out (may be NULL) gets each net's interaction
+ * count.  Copies only 16 bytes per net to the host. */
+inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* values_out,
+                               uint64_t* interactions_out);
 
 /* Per-net counters; live and residual agents come from the readback
  * snapshot. */

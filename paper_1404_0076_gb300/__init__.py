@@ -114,6 +114,12 @@ class Evaluator:
     def readback_nat(self, net_id: int) -> tuple[int, int]:
         return capi_lazy.inet_readback_nat(self.ctx, net_id)
 
+    def pending(self, net_ids) -> list[int]:
+        return capi_lazy.inet_net_pending(self.ctx, list(net_ids))
+
+    def readback_nats(self, net_ids):
+        return capi_lazy.inet_readback_nats(self.ctx, list(net_ids))
+
     def net_info(self, net_id: int) -> dict:
         return capi_lazy.inet_net_info(self.ctx, net_id)
 

@@ -40,7 +40,8 @@ EXPORTED = [
     "inet_workspace_bytes", "inet_create", "inet_attach_workspace", "inet_destroy",
     "inet_load_rules", "inet_rule_count", "inet_rule_info", "inet_load_net", "inet_reduce",
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
-    "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into",
+    "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
+    "inet_readback_nats",
 ]
 
 
@@ -101,6 +102,9 @@ def _load():
         "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
         "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_net_info": ([P, C.c_int32, C.POINTER(inet_net_stats)], C.c_int32),
+        "inet_net_pending": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64)], C.c_int32),
+        "inet_readback_nats": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64),
+                                C.POINTER(C.c_uint64)], C.c_int32),
         "inet_trace": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_size_t, C.POINTER(C.c_size_t)],
                        C.c_int32),
         "inet_reset": ([P], C.c_int32),
@@ -223,6 +227,23 @@ def inet_net_info(ctx, net_id: int) -> dict:
     return {"status": STATUS_NAMES.get(s.status, s.status), "reduced": bool(s.reduced),
             "interactions": s.interactions, "pending_pairs": s.pending_pairs,
             "live_agents": s.live_agents, "residual_agents": s.residual_agents}
+
+
+def inet_net_pending(ctx, net_ids) -> list[int]:
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    out = (C.c_uint64 * max(1, len(net_ids)))()
+    _check(ctx, LIB.inet_net_pending(ctx, ids, len(net_ids), out))
+    return list(out[:len(net_ids)])
+
+
+def inet_readback_nats(ctx, net_ids) -> tuple[list[int | None], list[int]]:
+    """(values, interactions); a value is None when the interface is not a numeral."""
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    vals = (C.c_uint64 * max(1, len(net_ids)))()
+    ints = (C.c_uint64 * max(1, len(net_ids)))()
+    _check(ctx, LIB.inet_readback_nats(ctx, ids, len(net_ids), vals, ints))
+    none = (1 << 64) - 1
+    return [None if v == none else v for v in vals[:len(net_ids)]], list(ints[:len(net_ids)])
 
 
 def inet_trace(ctx) -> tuple[list[int], list[int]]:

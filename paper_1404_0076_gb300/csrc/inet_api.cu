@@ -20,6 +20,7 @@ using namespace inet;
 namespace {
 
 constexpr uint32_t kTraceCap = 1u << 20;
+constexpr uint32_t kReadChunk = 1u << 16;  // nets per device walk of inet_readback_nats
 constexpr uint64_t kDefaultAgents = 1ull << 22;
 constexpr uint64_t kDefaultVars = 1ull << 22;
 constexpr uint64_t kDefaultPairs = 1ull << 21;
@@ -30,8 +31,8 @@ constexpr uint32_t kMaxSolo = 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Layout {
-  size_t ctrl, node, var, front0, front1, afree, vfree, netctr, netstat, hist, table, tmpl, arity,
-      trace_front, trace_live, total;
+  size_t ctrl, node, var, front0, front1, qseq, afree, vfree, netctr, netstat, hist, table, tmpl, arity,
+      trace_front, trace_live, rb_root, rb_val, total;
 };
 
 inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
@@ -59,6 +60,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.var = take(sizeof(uint32_t) * c.max_vars);
   L.front0 = take(sizeof(Pair) * c.max_pairs);
   L.front1 = take(sizeof(Pair) * c.max_pairs);
+  L.qseq = take(sizeof(unsigned long long) * c.max_pairs);
   L.afree = take(sizeof(uint32_t) * c.max_agents);
   L.vfree = take(sizeof(uint32_t) * c.max_vars);
   L.netctr = take(sizeof(unsigned long long) * c.max_nets);
@@ -69,6 +71,8 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.arity = take(kMaxLabels);
   L.trace_front = take(sizeof(long long) * kTraceCap);
   L.trace_live = take(sizeof(long long) * kTraceCap);
+  L.rb_root = take(sizeof(uint32_t) * kReadChunk);
+  L.rb_val = take(sizeof(unsigned long long) * kReadChunk);
   L.total = take(0) + 256;
   return L;
 }
@@ -181,6 +185,7 @@ void fill_dev(inet_ctx* ctx) {
   d.var = at<uint32_t>(ctx, L.var);
   d.front[0] = at<Pair>(ctx, L.front0);
   d.front[1] = at<Pair>(ctx, L.front1);
+  d.qseq = at<unsigned long long>(ctx, L.qseq);
   d.afree = at<uint32_t>(ctx, L.afree);
   d.vfree = at<uint32_t>(ctx, L.vfree);
   d.netctr = at<unsigned long long>(ctx, L.netctr);
@@ -837,6 +842,54 @@ inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out
   return INET_OK;
 }
 
+inet_status inet_net_pending(const inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* pending_out) {
+  if (!ctx || n < 0 || (n > 0 && (!net_ids || !pending_out))) return INET_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; i++) {
+    const int32_t id = net_ids[i];
+    if (id < 0 || (size_t)id >= ctx->nets.size() || !ctx->nets[(size_t)id].used) return INET_ERR_INVALID_ARG;
+    const NetRec& nr = ctx->nets[(size_t)id];
+    pending_out[i] = nr.started ? (ctx->h_netctr[(size_t)id] >> kNetPairShift) : nr.pairs.size();
+  }
+  return INET_OK;
+}
+
+inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* values_out,
+                               uint64_t* interactions_out) {
+  if (!ctx || n < 0 || (n > 0 && (!net_ids || !values_out))) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (n == 0) return INET_OK;
+  std::vector<uint32_t> roots((size_t)n);
+  for (int32_t i = 0; i < n; i++) {
+    inet_status s = check_net(ctx, net_ids[i]);
+    if (s) return s;
+    const NetRec& nr = ctx->nets[(size_t)net_ids[i]];
+    roots[(size_t)i] = nr.iface.size() == 1 ? nr.iface[0] : kEmpty;
+    if (interactions_out) interactions_out[i] = ctx->h_netctr[(size_t)net_ids[i]] & kNetIntMask;
+  }
+  auto si = ctx->rules.index.find("S");
+  auto zi = ctx->rules.index.find("Z");
+  if (si == ctx->rules.index.end() || zi == ctx->rules.index.end()) {
+    for (int32_t i = 0; i < n; i++) values_out[i] = ~0ull;
+    return INET_OK;
+  }
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  if ((s = upload_staged(ctx))) return s;
+  // roots in, values out, kReadChunk nets at a time
+  for (int32_t off = 0; off < n; off += (int32_t)kReadChunk) {
+    const int32_t m = std::min<int32_t>(n - off, (int32_t)kReadChunk);
+    uint32_t* droot = at<uint32_t>(ctx, ctx->lay.rb_root);
+    unsigned long long* dval = at<unsigned long long>(ctx, ctx->lay.rb_val);
+    CK(h2d(ctx, droot, roots.data() + off, sizeof(uint32_t) * (size_t)m));
+    k_read_nats<<<(m + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, droot, (uint32_t)m, si->second, zi->second, dval);
+    CK(cudaGetLastError());
+    CK(d2h(ctx, values_out + off, dval, sizeof(unsigned long long) * (size_t)m));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return INET_OK;
+}
+
 inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out) {
   if (!ctx || !out) return INET_ERR_INVALID_ARG;
   inet_status s = check_net(ctx, net_id);
@@ -1065,6 +1118,7 @@ extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void
   d.var = vars;
   d.front[0] = reinterpret_cast<Pair*>(fx + kFxFront0);
   d.front[1] = reinterpret_cast<Pair*>(fx + kFxFront1);
+  d.qseq = nullptr;  // no asynchronous launch here
   d.afree = reinterpret_cast<uint32_t*>(fx + kFxAfree);
   d.vfree = reinterpret_cast<uint32_t*>(fx + kFxVfree);
   d.netctr = reinterpret_cast<unsigned long long*>(fx + kFxNetctr);

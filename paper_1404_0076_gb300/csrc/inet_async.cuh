@@ -6,14 +6,16 @@
 // on its own, each lane holding at most one active pair.  An interaction
 // that creates active pairs keeps the first as the lane's next pair, so a
 // sequential chain of interactions never leaves its lane; further pairs go
-// to a FIFO of tickets that idle lanes claim.  The loop ends when no active
+// to a FIFO of tickets that idle lanes claim: a bounded ring whose cells
+// carry a 64-bit sequence number each, so that a producer and a consumer
+// of the same cell in different laps can never be confused.  The loop ends when no active
 // pair is left anywhere (the count of pairs in flight reaches zero), as in
 // Sec. 3.6; a time slice or an error instead drains every pair back to a
 // frontier buffer so that the host can resume.
 //
 // Ordering without barriers: a lane writes its new agent records, then
 // publishes references to them only through release operations (the
-// acq_rel exchange on a name slot, the release store of a queue slot);
+// acq_rel exchange on a name slot, the release store of a cell's sequence);
 // every lane that learns of an agent does so through the matching acquire,
 // so the records it then loads are the ones written.
 #pragma once
@@ -26,7 +28,6 @@ constexpr int kAStack = 128;   // per-warp stack of free agent slots
 constexpr int kVStack = 128;   // per-warp stack of free name slots
 constexpr int kVStageW = 64;   // names freed while linking, per warp
 constexpr int kRefill = 32;    // slots fetched for the warp's stack when it runs dry
-constexpr unsigned long long kQEmpty = ~0ull;
 constexpr unsigned long long kNoTicket = ~0ull;
 
 struct WarpMem {
@@ -59,12 +60,12 @@ __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned lon
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Queue slot encoding: the pair with bit 31 of `a` = lap parity of the
-// ticket (ticket / capacity), so a waiter never takes a previous lap's pair.
-__device__ __forceinline__ bool q_ready(unsigned long long v, unsigned long long ticket, unsigned long long cap) {
-  if (v == kQEmpty) return false;
-  return (((uint32_t)v) >> 31) == (uint32_t)((ticket / cap) & 1ull);
-}
+// Ticket queue: ticket t lives in cell t % cap, whose sequence number
+// moves t -> t + 1 (the producer wrote the pair) -> t + cap (the consumer
+// took it, so the cell is free for ticket t + cap).  A producer writes only
+// when the sequence equals its own ticket, a consumer takes only at its
+// ticket + 1; both compare all 64 bits, so no lap can be mistaken for
+// another however far ahead tickets were claimed.
 
 // ->com for the asynchronous kernel (the chase after a second arrival):
 // link_eq with freed name slots staged per warp.  The lane has fenced its
@@ -397,13 +398,36 @@ __device__ __forceinline__ void exit_pair(const Dev& d, Pair p) {
   }
 }
 
-// Bounded wait for a ticket's slot; returns false on timeout.
-__device__ __forceinline__ bool wait_slot(const Dev& d, const unsigned long long* slot, unsigned long long ticket,
-                                          unsigned long long cap, unsigned long long* v) {
+// A lane that claimed a ticket takes its pair as soon as it is published
+// and frees the cell for the next lap.  Every wait of the asynchronous loop
+// does this too, so a producer waiting for a cell never waits on a lane
+// that is itself waiting.
+__device__ __forceinline__ void poll_ticket(const Dev& d, const Pair* Q, bool& have, unsigned long long& ticket,
+                                            unsigned long long tslot, uint32_t& pa, uint32_t& pb) {
+  if (!have && ticket != kNoTicket) {
+    unsigned long long* sq = d.qseq + tslot;
+    if (ld_acquire64(sq) == ticket + 1) {
+      const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long*>(Q + tslot));
+      st_release64(sq, ticket + d.cap_pairs);
+      pa = (uint32_t)v;
+      pb = (uint32_t)(v >> 32);
+      have = true;
+      ticket = kNoTicket;
+    }
+  }
+}
+
+// Bounded wait for ticket t's pair (when no producer runs any more);
+// returns false on timeout.
+__device__ __forceinline__ bool wait_ticket(const Dev& d, const Pair* Q, unsigned long long t, Pair* out) {
+  const unsigned long long s = t % d.cap_pairs;
   const unsigned long long t0 = globaltimer();
   for (uint32_t spin = 0;; spin++) {
-    *v = ld_acquire64(slot);
-    if (q_ready(*v, ticket, cap)) return true;
+    if (ld_acquire64(d.qseq + s) == t + 1) {
+      const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long*>(Q + s));
+      *out = Pair{(uint32_t)v, (uint32_t)(v >> 32)};
+      return true;
+    }
     __nanosleep(64);
     if ((spin & 63) == 63 && globaltimer() - t0 > d.timeout_ns) {
       set_error(d.ctrl, INET_ERR_TIMEOUT, 6);
@@ -440,7 +464,6 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
   bool have = false;
   uint32_t pa = 0, pb = 0;
   unsigned long long ticket = kNoTicket, tslot = 0;
-  uint32_t tlap = 0;
   long long live = 0;
   uint32_t nap = 0;
   bool stop = false, finished = false;
@@ -484,38 +507,19 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
       }
       k = __shfl_sync(kFull, k, 0);
       if (k) {
-        unsigned long long bm = 0, bl = 0;
-        if (lane == 0) {
-          bm = base % cap;
-          bl = (base / cap) & 1ull;
-        }
+        unsigned long long bm = 0;
+        if (lane == 0) bm = base % cap;
         base = __shfl_sync(kFull, base, 0);
         bm = __shfl_sync(kFull, bm, 0);
-        bl = __shfl_sync(kFull, bl, 0);
         const unsigned rank = __popc(want & lanemask_lt());
         if (((want >> lane) & 1u) && rank < k) {
           ticket = base + rank;
           tslot = bm + rank;
-          tlap = (uint32_t)bl;
-          if (tslot >= cap) {
-            tslot -= cap;
-            tlap ^= 1u;
-          }
+          if (tslot >= cap) tslot %= cap;
         }
       }
     }
-    // poll claimed tickets
-    if (!have && ticket != kNoTicket) {
-      unsigned long long* slot = reinterpret_cast<unsigned long long*>(Q + tslot);
-      const unsigned long long v = ld_acquire64(slot);
-      if (v != kQEmpty && (((uint32_t)v) >> 31) == tlap) {
-        *reinterpret_cast<volatile unsigned long long*>(slot) = kQEmpty;
-        pa = ((uint32_t)v) & 0x7FFFFFFFu;
-        pb = (uint32_t)(v >> 32);
-        have = true;
-        ticket = kNoTicket;
-      }
-    }
+    poll_ticket(d, Q, have, ticket, tslot, pa, pb);
     const unsigned act = __ballot_sync(kFull, have);
     if (!act) {
       // idle: the loop is over when no pair is left anywhere
@@ -543,7 +547,11 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
     // pairs in flight: each new pair beyond a lane's own next one joins
     // before it is published (lane 0 waits until the increment is performed,
     // so no consumer's decrement can overtake it); each pair that produced
-    // nothing leaves afterwards
+    // nothing leaves afterwards.  At most cap pairs may be in flight, the
+    // capacity of the frontier that a stop drains them to; beyond it the
+    // arena is full.  Under that bound the queue slot a producer needs is
+    // held by a claimed ticket whenever it is still occupied: an unclaimed
+    // one would put every later ticket, and so more than cap pairs, in flight.
     long long grow = extra, shrink = had && np == 0 ? -1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -551,8 +559,9 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
       shrink += __shfl_xor_sync(kFull, shrink, o);
     }
     if (lane == 0 && grow) {
-      const unsigned long long r = atomicAdd(reinterpret_cast<unsigned long long*>(&c->inflight), (unsigned long long)grow);
-      asm volatile("" ::"l"(r));
+      const long long r =
+          (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&c->inflight), (unsigned long long)grow);
+      if (r + grow > (long long)cap) set_error(c, INET_ERR_ARENA_FULL, 9);
     }
     __syncwarp();
     {
@@ -582,32 +591,47 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
         }
         const unsigned toq = totx - local;
         if (toq) {
-          unsigned long long qm = 0, ql = 0;
+          unsigned long long qb = 0, qm = 0;
           if (lane == 0) {
-            const unsigned long long qb = atomicAdd(&c->q_tail, (unsigned long long)toq);
+            qb = atomicAdd(&c->q_tail, (unsigned long long)toq);
             qm = qb % cap;
-            ql = (qb / cap) & 1ull;
           }
+          qb = __shfl_sync(kFull, qb, 0);
           qm = __shfl_sync(kFull, qm, 0);
-          ql = __shfl_sync(kFull, ql, 0);
-          for (unsigned j = lane; j < toq; j += 32) {
+          for (unsigned j0 = 0; j0 < toq; j0 += 32) {
+            const unsigned j = j0 + (unsigned)lane;
+            bool pend = j < toq;
+            const unsigned long long tk = qb + j;
             unsigned long long si = qm + j;
-            uint32_t lap = (uint32_t)ql;
-            if (si >= cap) {
-              si -= cap;
-              lap ^= 1u;
-            }
-            unsigned long long* slot = reinterpret_cast<unsigned long long*>(Q + si);
+            if (si >= cap) si %= cap;
+            const Pair p = pend ? W.xl[local + j] : Pair{0, 0};
             const unsigned long long t0 = globaltimer();
-            while (ld_volatile64(slot) != kQEmpty) {  // the previous lap's pair is not taken yet
+            for (uint32_t spin = 0;; spin++) {
+              // written once the cell's previous pair (ticket tk - cap) is taken
+              if (pend && ld_acquire64(d.qseq + si) == tk) {
+                __stcg(reinterpret_cast<unsigned long long*>(Q + si),
+                       (unsigned long long)p.a | ((unsigned long long)p.b << 32));
+                st_release64(d.qseq + si, tk + 1);
+                pend = false;
+              }
+              poll_ticket(d, Q, have, ticket, tslot, pa, pb);
+              if (!__any_sync(kFull, pend)) break;
               __nanosleep(64);
-              if (globaltimer() - t0 > d.timeout_ns) {
-                set_error(c, INET_ERR_TIMEOUT, 7);
-                break;
+              if ((spin & 15) == 15) {
+                // after a fatal error (the arena is poisoned) or the time
+                // limit, pairs not yet written are given up
+                uint32_t give = 0;
+                if (lane == 0) {
+                  if (ld_volatile((const uint32_t*)&c->fatal)) {
+                    give = 1;
+                  } else if (globaltimer() - t0 > d.timeout_ns) {
+                    set_error(c, INET_ERR_TIMEOUT, 7);
+                    give = 1;
+                  }
+                }
+                if (__shfl_sync(kFull, give, 0)) break;
               }
             }
-            const Pair p = W.xl[local + j];
-            st_release64(slot, (unsigned long long)(p.a | (lap << 31)) | ((unsigned long long)p.b << 32));
           }
         }
         __syncwarp();
@@ -628,25 +652,36 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
     if (lane == 0) {
       __threadfence();
       atomicAdd(&c->quiesce, 1u);
-      const unsigned long long t0 = globaltimer();
-      while (ld_volatile(&c->quiesce) < total_warps) {
-        __nanosleep(256);
-        if (globaltimer() - t0 > d.timeout_ns) {
+    }
+    __syncwarp();
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+      poll_ticket(d, Q, have, ticket, tslot, pa, pb);  // producers still running may wait for this lane's slot
+      uint32_t done = 0;
+      if (lane == 0) {
+        if (ld_volatile(&c->quiesce) >= total_warps) {
+          done = 1;
+        } else if (globaltimer() - t0 > d.timeout_ns) {
           set_error(c, INET_ERR_TIMEOUT, 8);
           ok = 0;
-          break;
+          done = 1;
         }
       }
+      if (__shfl_sync(kFull, done, 0)) break;
+      __nanosleep(256);
+    }
+    if (lane == 0) {
       __threadfence();
+      if (ld_volatile((const uint32_t*)&c->fatal)) ok = 0;  // poisoned: nothing to keep
     }
     ok = __shfl_sync(kFull, ok, 0);
     if (ok) {
       const unsigned long long qt = ld_volatile64(&c->q_tail);
       if (!have && ticket != kNoTicket && ticket < qt) {
-        unsigned long long v;
-        if (wait_slot(d, reinterpret_cast<unsigned long long*>(Q + ticket % cap), ticket, cap, &v)) {
-          pa = ((uint32_t)v) & 0x7FFFFFFFu;
-          pb = (uint32_t)(v >> 32);
+        Pair p;
+        if (wait_ticket(d, Q, ticket, &p)) {
+          pa = p.a;
+          pb = p.b;
           have = true;
         }
       }
@@ -656,9 +691,8 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
       const uint32_t gw = blockIdx.x * (blockDim.x / 32) + (uint32_t)wid;
       for (unsigned long long tk = qh + (unsigned long long)gw * 32 + lane; tk < qt;
            tk += (unsigned long long)total_warps * 32) {
-        unsigned long long v;
-        if (wait_slot(d, reinterpret_cast<unsigned long long*>(Q + tk % cap), tk, cap, &v))
-          exit_pair(d, Pair{((uint32_t)v) & 0x7FFFFFFFu, (uint32_t)(v >> 32)});
+        Pair p;
+        if (wait_ticket(d, Q, tk, &p)) exit_pair(d, p);
       }
     }
   }
@@ -680,14 +714,13 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
     if (hist[i]) atomicAdd(&d.rule_hist[i], (unsigned long long)hist[i]);
 }
 
-// Before an asynchronous launch: mark every queue slot past the current
-// frontier empty.
+// Before an asynchronous launch: the current frontier's pairs are tickets
+// 0 .. n0-1, already written; every other cell waits for its first ticket.
 __global__ void k_async_fill(Dev d) {
   const uint32_t n0 = min(d.ctrl->fcount[d.qcur], d.cap_pairs);
-  unsigned long long* q = reinterpret_cast<unsigned long long*>(d.front[d.qcur]);
-  for (unsigned long long i = n0 + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < d.cap_pairs;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < d.cap_pairs;
        i += (unsigned long long)gridDim.x * blockDim.x)
-    q[i] = kQEmpty;
+    d.qseq[i] = i < n0 ? i + 1 : i;
 }
 
 // Before an asynchronous launch (one thread): publish the rings, make the

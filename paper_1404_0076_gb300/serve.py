@@ -1,0 +1,199 @@
+"""Continuous-batching request loop over the evaluator's C ABI.
+
+Requests (one net each) are admitted as they arrive, while the arena they go
+to has room for them by an estimate of their footprint; every admitted net
+joins the frontier of the nets already in flight (inet_stage), and the
+device runs the asynchronous loop in bounded epochs (slice_us), between
+which finished nets are harvested (inet_net_pending, inet_readback_nats)
+and new ones admitted.  Requests therefore overlap on the device with
+whatever is in flight; each result is independent of the mix because nets
+share no agent and interactions are local (Sec. 2.1).
+
+Memory: two arenas are used in turn.  New requests go to the active one
+while its estimated use fits; when it is full, admission switches to the
+other, which is reset first once its last request has finished (its
+arena then holds only results already read back).  No arena ever needs a
+scan to free a finished net.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass
+
+
+@dataclass
+class Finished:
+    rid: int
+    arrival: float      # seconds, on the server clock
+    admitted: float
+    finished: float
+    value: int | None   # numeral result, None if the interface is not S^k(Z)
+    interactions: int
+    status: str = "OK"
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def agents_in(text: str) -> int:
+    """Agent symbols in a net's text (upper-case initials)."""
+    n = 0
+    prev = " "
+    for ch in text:
+        if ch.isupper() and not (prev.isalnum() or prev == "_"):
+            n += 1
+        prev = ch
+    return n
+
+
+def default_footprint(text: str, size: int) -> int:
+    """Estimated peak agent slots of a request: its agents plus a share per
+    expected interaction (numerals built by the net stay alive)."""
+    return 2 * agents_in(text) + size + 64
+
+
+class Server:
+    def __init__(self, rules: str, device: int = 0, budget_bytes: int = 2 << 30, epoch_us: int = 1000,
+                 max_nets: int = 1 << 15, max_pairs: int = 1 << 22, block: int = 0, grid: int = 0,
+                 footprint=default_footprint, make_evaluator=None):
+        share = budget_bytes // 2
+        # per agent slot: 16-byte record + 4-byte ring entry; per name slot: 4 + 4;
+        # frontier: 2 x 8 bytes per pair
+        rest = max(share - 16 * max_pairs, 1 << 20)
+        self.max_agents = int(min(rest * 3 // 4 // 20, (1 << 30) - 1))
+        self.max_vars = int(min(rest // 4 // 8, (1 << 30) - 1))
+        if make_evaluator is None:
+            from . import Evaluator
+
+            def make_evaluator():
+                return Evaluator(device, max_agents=self.max_agents, max_vars=self.max_vars,
+                                 max_pairs=max_pairs, max_nets=max_nets)
+        self.ctx = [make_evaluator(), make_evaluator()]
+        for ev in self.ctx:
+            ev.load_rules(rules)
+        self.max_nets = max_nets
+        self.epoch_us = epoch_us
+        self.block, self.grid = block, grid
+        self.footprint = footprint
+        self.active = 0
+        self.used = [0, 0]          # estimated agent slots committed per arena
+        self.nets = [0, 0]          # nets loaded per arena since its reset
+        self.inflight = [{}, {}]    # arena -> {net id: (rid, arrival, admitted)}
+        self.unstaged = [[], []]    # admitted nets not yet handed to the device
+        self.epochs = 0
+        self.switches = 0
+
+    def close(self):
+        for ev in self.ctx:
+            ev.close()
+
+    # -- admission -------------------------------------------------------
+    def _room(self, k: int, need: int) -> bool:
+        return self.used[k] + need <= self.max_agents and self.nets[k] < self.max_nets
+
+    def _reset(self, k: int):
+        self.ctx[k].reset()
+        self.used[k] = 0
+        self.nets[k] = 0
+        self.unstaged[k] = []
+
+    def try_admit(self, rid: int, text: str, size: int, arrival: float, now: float) -> bool:
+        need = self.footprint(text, size)
+        if need > self.max_agents:
+            raise ValueError(f"request {rid} needs about {need} agent slots; an arena holds {self.max_agents}")
+        k = self.active
+        if not self._room(k, need):
+            other = 1 - k
+            if self.inflight[other]:
+                return False                      # both arenas busy: wait
+            self._reset(other)
+            self.active = k = other
+            self.switches += 1
+        ev = self.ctx[k]
+        nid = ev.load_net(text)
+        self.unstaged[k].append(nid)
+        self.used[k] += need
+        self.nets[k] += 1
+        self.inflight[k][nid] = (rid, arrival, now)
+        return True
+
+    # -- device epochs and harvest ------------------------------------------
+    def epoch(self, now_fn) -> list[Finished]:
+        done = []
+        for k in (0, 1):
+            if self.unstaged[k]:
+                self.ctx[k].stage(self.unstaged[k])   # one upload for every net admitted since
+                self.unstaged[k] = []
+            if not self.inflight[k]:
+                continue
+            st = self.ctx[k].reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
+                                    check=False)
+            self.epochs += 1
+            ids = list(self.inflight[k].keys())
+            if st["status"] not in ("OK", "STEP_LIMIT", "NO_RULE"):
+                # a fatal error poisons the arena: every request in it fails
+                t = now_fn()
+                for nid in ids:
+                    rid, arr, adm = self.inflight[k].pop(nid)
+                    done.append(Finished(rid, arr, adm, t, None, 0, st["status"]))
+                self._reset(k)
+                continue
+            pend = self.ctx[k].pending(ids)
+            fin = [nid for nid, p in zip(ids, pend) if p == 0]
+            if fin:
+                vals, ints = self.ctx[k].readback_nats(fin)
+                t = now_fn()
+                for nid, v, n in zip(fin, vals, ints):
+                    rid, arr, adm = self.inflight[k].pop(nid)
+                    done.append(Finished(rid, arr, adm, t, v, n))
+        return done
+
+    def busy(self) -> bool:
+        return bool(self.inflight[0] or self.inflight[1])
+
+    def serve(self, requests, time_scale: float = 1.0, max_wall_s: float = math.inf) -> list[Finished]:
+        """Runs `requests` (objects with .arrival_s, .net, .size) to the end.
+        Arrivals are replayed on the wall clock, scaled by time_scale."""
+        reqs = sorted(enumerate(requests), key=lambda ir: ir[1].arrival_s)
+        pending = collections.deque(reqs)
+        t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        out: list[Finished] = []
+        waiting = collections.deque()
+        while pending or waiting or self.busy():
+            t = now()
+            if t > max_wall_s:
+                break
+            while pending and pending[0][1].arrival_s * time_scale <= t:
+                waiting.append(pending.popleft())
+            while waiting:
+                rid, r = waiting[0]
+                if not self.try_admit(rid, r.net, r.size, r.arrival_s * time_scale, now()):
+                    break
+                waiting.popleft()
+            if self.busy():
+                out.extend(self.epoch(now))
+            elif pending and not waiting:
+                time.sleep(max(0.0, min(0.001, pending[0][1].arrival_s * time_scale - now())))
+        return out
+
+
+def summarize(done: list[Finished], wall_s: float) -> dict:
+    lat = sorted(f.latency for f in done)
+
+    def pct(p):
+        if not lat:
+            return None
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+
+    ints = sum(f.interactions for f in done)
+    return {"requests": len(done), "p50_ms": 1e3 * pct(50) if lat else None, "p99_ms": 1e3 * pct(99) if lat else None,
+            "mean_ms": 1e3 * sum(lat) / len(lat) if lat else None, "interactions": ints,
+            "interactions_per_s": ints / wall_s if wall_s > 0 else None,
+            "failed": sum(1 for f in done if f.status != "OK")}

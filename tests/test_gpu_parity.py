@@ -7,6 +7,7 @@ against the oracle's maximally parallel "rounds" schedule.
 """
 import json
 import os
+import time
 
 import pytest
 
@@ -323,9 +324,100 @@ def test_async_no_rule_and_arena_full(orc):
     ev = make_ev(max_agents=400, max_vars=400, max_pairs=256)
     ev.load_rules(R)
     i = ev.load_net(W.fib_net(12))
+    t0 = time.perf_counter()
     assert ev.reduce([i], mode="async", check=False)["status"] == "ARENA_FULL"
+    # the error ends the loop at once, not after a bounded wait runs out
+    assert time.perf_counter() - t0 < 2.0
     ev.reset()
     j = ev.load_net(W.add_net(4, 4))
     ev.reduce([j], mode="async")
     assert ev.readback_nat(j) == (8, 5)
+    ev.close()
+
+
+def test_pending_and_batched_nat_readback(orc):
+    # inet_net_pending counts a net's unreduced pairs; inet_readback_nats
+    # reads many numerals at once and marks an interface that is not S^k(Z)
+    nets = [W.fib_net(16), W.add_net(7, 9), W.mul_net(9, 8), "< a, b | Add(a, b) = Z >", W.ack_net(2, 4)]
+    o = orc.run(R, nets)
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    ev.stage(ids)
+    assert ev.pending(ids) == [ev.net_info(i)["pending_pairs"] for i in ids]
+    st = ev.reduce([], mode="async", slice_us=50, check=False)
+    while st["status"] == "STEP_LIMIT":
+        pend = ev.pending(ids)
+        assert all(p >= 0 for p in pend)
+        st = ev.reduce([], mode="async", slice_us=50, check=False)
+    assert st["status"] == "OK"
+    assert ev.pending(ids) == [0] * len(ids)
+    vals, ints = ev.readback_nats(ids)
+    assert ints == [x["interactions"] for x in o]
+    assert vals == [x["nat"] for x in o]
+    assert vals[3] is None
+    # the batched walk agrees with the one-net readback, also in another order
+    rev = ids[::-1]
+    assert ev.readback_nats(rev)[0] == vals[::-1]
+    for i, v in zip(ids, vals):
+        if v is not None:
+            assert ev.readback_nat(i)[0] == v
+    assert ev.readback_nats([]) == ([], [])
+    ev.close()
+
+
+@pytest.mark.parametrize("grid,block", [(1, 32), (0, 0)])
+def test_async_queue_wraps_near_capacity(orc, grid, block):
+    # in-flight pairs hold two live agents each, so with these nets (at
+    # most about 900 live agents at once under any schedule) 512 pairs
+    # always suffice, while the ticket queue of 512 slots wraps several
+    # times; producers then wait for slots of the previous lap
+    nets = [W.fib_net(12), W.ack_net(3, 4)]
+    o = orc.run(R, nets)
+    ev = make_ev(max_pairs=512)
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    t0 = time.perf_counter()
+    st = ev.reduce(ids, mode="async", grid=grid, block=block)
+    assert time.perf_counter() - t0 < 5.0
+    assert st["status"] == "OK"
+    for k, i in enumerate(ids):
+        assert ev.readback(i) == o[k]["result"]
+        assert ev.net_info(i)["interactions"] == o[k]["interactions"]
+    ev.close()
+
+
+def test_async_pair_capacity_is_an_error_not_a_wait(orc):
+    # more pairs in flight than the frontier holds ends the loop with
+    # ARENA_FULL at once; if this schedule stayed below the capacity the
+    # results must be exact
+    nets = [W.fib_net(14)]
+    ev = make_ev(max_pairs=64)
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    t0 = time.perf_counter()
+    st = ev.reduce(ids, mode="async", check=False)
+    assert time.perf_counter() - t0 < 2.0
+    assert st["status"] in ("ARENA_FULL", "OK")
+    if st["status"] == "OK":
+        o = orc.run(R, nets)
+        assert ev.readback(ids[0]) == o[0]["result"]
+    ev.reset()
+    j = ev.load_net(W.add_net(3, 4))
+    ev.reduce([j], mode="async")
+    assert ev.readback_nat(j) == (7, 4)
+    ev.close()
+
+
+def test_batched_nat_readback_leaves_the_trace(orc):
+    nets = [W.add_net(20, 5), W.mul_net(6, 7)]
+    o = orc.run(R, nets, mode="rounds")
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    ev.reduce(ids, mode="persistent", trace=True)
+    tr = ev.trace()
+    assert tr[0] == summed_rounds(o)
+    assert ev.readback_nats(ids)[0] == [25, 42]
+    assert ev.trace() == tr
     ev.close()

@@ -1,0 +1,150 @@
+"""The continuous-batching request loop (paper_1404_0076_gb300/serve.py).
+
+CPU: the admission and arena-switching logic against a fake evaluator.
+GPU: a stream of mixed requests whose results, computed while they overlap
+on the device, must equal each request reduced alone (the oracle).
+"""
+import random
+from dataclasses import dataclass
+
+import pytest
+
+import workloads as W
+from paper_1404_0076_gb300.serve import Server, default_footprint, summarize
+
+
+@dataclass
+class Req:
+    arrival_s: float
+    net: str
+    size: int
+
+
+class FakeEvaluator:
+    """Completes each net after `size` epochs; counts resets."""
+
+    def __init__(self):
+        self.left = {}
+        self.value = {}
+        self.next_id = 0
+        self.resets = 0
+        self.staged = set()
+
+    def load_rules(self, text):
+        pass
+
+    def load_net(self, text):
+        i = self.next_id
+        self.next_id += 1
+        size = int(text.split(":")[1])
+        self.left[i] = size
+        self.value[i] = size * 10
+        return i
+
+    def stage(self, ids):
+        self.staged.update(ids)
+
+    def reduce(self, ids, mode, slice_us, block, grid, check):
+        for i in list(self.staged):
+            if self.left[i] > 0:
+                self.left[i] -= 1
+        return {"status": "OK" if all(v == 0 for v in self.left.values()) else "STEP_LIMIT"}
+
+    def pending(self, ids):
+        return [self.left[i] for i in ids]
+
+    def readback_nats(self, ids):
+        return [self.value[i] for i in ids], [self.value[i] // 10 for i in ids]
+
+    def reset(self):
+        self.resets += 1
+        self.left.clear()
+        self.value.clear()
+        self.staged.clear()
+        self.next_id = 0
+
+    def close(self):
+        pass
+
+
+def test_admission_and_arena_switching_on_cpu():
+    fakes = []
+
+    def make():
+        f = FakeEvaluator()
+        fakes.append(f)
+        return f
+
+    srv = Server("", budget_bytes=64 << 20, max_pairs=1 << 10, make_evaluator=make,
+                 footprint=lambda text, size: 10_000)
+    cap = srv.max_agents // 10_000          # requests one arena admits
+    assert cap >= 2
+    reqs = [Req(0.0, f"net:{1 + (i % 5)}", 1 + (i % 5)) for i in range(4 * cap + 3)]
+    done = srv.serve(reqs)
+    assert len(done) == len(reqs)
+    assert sorted(d.rid for d in done) == list(range(len(reqs)))
+    for d in done:
+        size = 1 + (d.rid % 5)
+        assert d.value == 10 * size and d.interactions == size
+        assert d.finished >= d.admitted >= d.arrival >= 0
+    assert srv.switches >= 2
+    assert sum(f.resets for f in fakes) >= 2
+    s = summarize(done, 1.0)
+    assert s["requests"] == len(reqs) and s["p99_ms"] >= s["p50_ms"]
+
+
+def test_oversized_request_is_refused_on_cpu():
+    srv = Server("", budget_bytes=64 << 20, max_pairs=1 << 10, make_evaluator=FakeEvaluator,
+                 footprint=lambda text, size: 1 << 40)
+    with pytest.raises(ValueError):
+        srv.serve([Req(0.0, "net:1", 1)])
+
+
+def mixed_requests(n, seed=14040076 + 4):
+    rng = random.Random(seed)
+    out = []
+    t = 0.0
+    for _ in range(n):
+        t += rng.expovariate(20000.0)
+        f = rng.randrange(4)
+        if f == 0:
+            m, k = rng.randrange(0, 300), rng.randrange(0, 50)
+            out.append(Req(t, W.add_net(m, k), m + 1))
+        elif f == 1:
+            m, k = rng.randrange(0, 20), rng.randrange(0, 20)
+            out.append(Req(t, W.mul_net(m, k), 2 + m * (k + 3) + k * m * m // 2))
+        elif f == 2:
+            a, b = rng.choice([(1, 5), (2, 3), (2, 6), (3, 2), (3, 4)])
+            out.append(Req(t, W.ack_net(a, b), 25000))
+        else:
+            k = rng.randrange(0, 16)
+            out.append(Req(t, W.fib_net(k), 3000))
+    return out
+
+
+@pytest.mark.gpu
+def test_results_in_the_mix_equal_results_alone(oracle):
+    reqs = mixed_requests(600)
+    # an arena holding about a quarter of the stream's estimated footprint
+    # forces several arena switches while requests overlap
+    total = sum(default_footprint(r.net, r.size) for r in reqs)
+    max_pairs = 1 << 16
+    per_arena = max(total // 4, 4 * max(default_footprint(r.net, r.size) for r in reqs))
+    budget = 2 * (per_arena * 80 // 3 + 16 * max_pairs)
+    srv = Server(W.ARITH_RULES, budget_bytes=budget, epoch_us=300, max_pairs=max_pairs)
+    assert srv.max_agents < total // 2
+    try:
+        done = srv.serve(reqs)
+    finally:
+        srv.close()
+    assert len(done) == len(reqs)
+    alone = oracle.run(W.ARITH_RULES, [r.net for r in reqs], quiet=True, threads=8)
+    for d in sorted(done, key=lambda d: d.rid):
+        o = alone[d.rid]
+        assert d.status == "OK"
+        assert (d.value, d.interactions) == (o["nat"], o["interactions"]), d.rid
+    assert srv.switches >= 1
+    # requests overlapped on the device: some request was admitted while
+    # another one was still in flight
+    spans = sorted((d.admitted, d.finished) for d in done)
+    assert any(b[0] < a[1] for a, b in zip(spans, spans[1:]))
