@@ -205,6 +205,55 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --- serving ----------------------------------------------------------------------
+def expected_value(r) -> int:
+    """The numeral a serving request reduces to (closed forms)."""
+    if r.family == "add":
+        return r.params[0] + r.params[1]
+    if r.family == "mul":
+        return r.params[0] * r.params[1]
+    if r.family == "ack":
+        return W._ack(*r.params)
+    return W._fib_values(r.params[0] + 1)[r.params[0]]
+
+
+def serving_leg(args, local: int) -> dict:
+    """Continuous batching on the serving mix: the first --serve-requests
+    requests of the 100k-request Poisson stream (1000 requests/s), replayed
+    on the wall clock, then the same requests all at once (saturated).
+    Every result is checked against its closed form (value and exact
+    interaction count)."""
+    import dataclasses
+
+    from paper_1404_0076_gb300.serve import Server, summarize
+    reqs = W.config4()[: args.serve_requests]
+    expect = [expected_value(r) for r in reqs]
+    budget = args.serve_budget_gb << 30
+    srv = Server(W.ARITH_RULES, device=local, budget_bytes=budget, epoch_us=args.serve_epoch_us, max_pairs=1 << 23)
+    out = {"workload": "serving mix: Poisson arrivals at 1000 requests/s, one net each from add/mul/ack/fib, "
+                       "sizes lognormal (median 1e3 interactions, sigma 2.16, clipped to 1e7), seed 14040076+4",
+           "requests": len(reqs), "budget_bytes": budget, "arenas": 2, "epoch_us": args.serve_epoch_us,
+           "sample": f"first {len(reqs)} of the 100000-request stream"}
+    try:
+        srv.serve([dataclasses.replace(r, arrival_s=0.0) for r in reqs[:64]])  # warm-up
+        for name, scale in (("poisson", 1.0), ("saturated", 0.0)):
+            e0, s0 = srv.epochs, srv.switches
+            t0 = time.perf_counter()
+            done = srv.serve(reqs, time_scale=scale)
+            wall = time.perf_counter() - t0
+            rec = summarize(done, wall)
+            rec["wall_s"] = wall
+            rec["epochs"] = srv.epochs - e0
+            rec["arena_switches"] = srv.switches - s0
+            rec["wrong"] = sum(1 for d in done if d.status != "OK"
+                               or (d.value, d.interactions) != (expect[d.rid], reqs[d.rid].size))
+            out[name] = rec
+    finally:
+        srv.close()
+    out["offered_interactions_per_s"] = sum(r.size for r in reqs) / max(1e-9, reqs[-1].arrival_s)
+    return out
+
+
 # --- our arm ------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -220,6 +269,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-epoch-us", type=int, default=250)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -343,6 +396,10 @@ def main():
         cpu = {"value": ci / cs, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"whole workload once ({len(nets)} nets, {ci} interactions), {cores} threads"}
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_leg(args, local)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True,
@@ -352,7 +409,7 @@ def main():
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"independent batches, {world} rank(s)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "plain": plain}
+                "clocks": clk.summary(), "plain": plain, "serving": serving}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

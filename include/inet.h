@@ -217,6 +217,25 @@ inet_status inet_net_pending(const inet_ctx* ctx, const int32_t* net_ids, int32_
 inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* values_out,
                                uint64_t* interactions_out);
 
+/* inet_readback_nats() without blocking the caller or the main stream: the
+ * walk runs on a second stream of the context, after the work queued so far
+ * on the main stream and alongside later inet_reduce() calls (finished nets
+ * are never touched by the reduction of others, Sec. 2.1).  At most
+ * 65536 nets per batch and one batch in flight per context; inet_reset()
+ * waits for it and drops its results.  The nets should be finished
+ * (inet_net_pending() == 0); an unfinished net reads as not-a-numeral or as
+ * a partial count.  The paper has no counterpart: it serves a request loop
+ * that harvests results while the device keeps reducing. */
+inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int32_t n);
+
+/* Completes the batch begun last.  If it is done (wait != 0: once it is),
+ * copies its n values (as inet_readback_nats()) and interaction counts
+ * (interactions_out may be NULL) into arrays of at least `cap` entries, in
+ * begin order, and sets *n_out = n; otherwise sets *n_out = -1 and returns
+ * INET_OK.  INET_ERR_STATE when no batch is in flight. */
+inet_status inet_readback_nats_end(inet_ctx* ctx, int32_t wait, uint64_t* values_out, uint64_t* interactions_out,
+                                   int32_t cap, int32_t* n_out);
+
 /* Per-net counters; live and residual agents come from the readback
  * snapshot. */
 inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out);

@@ -120,6 +120,16 @@ class Evaluator:
     def readback_nats(self, net_ids):
         return capi_lazy.inet_readback_nats(self.ctx, list(net_ids))
 
+    def readback_nats_begin(self, net_ids) -> None:
+        """Starts a batched numeral readback that overlaps later reductions."""
+        capi_lazy.inet_readback_nats_begin(self.ctx, list(net_ids))
+
+    def readback_nats_end(self, wait: bool = False):
+        """(values, interactions) of the batch begun last, or None while it runs."""
+        if getattr(self, "_rb_bufs", None) is None:
+            self._rb_bufs = capi_lazy.readback_buffers()
+        return capi_lazy.inet_readback_nats_end(self.ctx, wait, self._rb_bufs)
+
     def net_info(self, net_id: int) -> dict:
         return capi_lazy.inet_net_info(self.ctx, net_id)
 

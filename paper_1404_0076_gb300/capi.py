@@ -41,8 +41,10 @@ EXPORTED = [
     "inet_load_rules", "inet_rule_count", "inet_rule_info", "inet_load_net", "inet_reduce",
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
-    "inet_readback_nats",
+    "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end",
 ]
+
+READ_CHUNK = 65536  # nets per non-blocking readback batch
 
 
 class inet_arena_cfg(C.Structure):
@@ -105,6 +107,9 @@ def _load():
         "inet_net_pending": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64),
                                 C.POINTER(C.c_uint64)], C.c_int32),
+        "inet_readback_nats_begin": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
+        "inet_readback_nats_end": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int32,
+                                    C.POINTER(C.c_int32)], C.c_int32),
         "inet_trace": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_size_t, C.POINTER(C.c_size_t)],
                        C.c_int32),
         "inet_reset": ([P], C.c_int32),
@@ -244,6 +249,27 @@ def inet_readback_nats(ctx, net_ids) -> tuple[list[int | None], list[int]]:
     _check(ctx, LIB.inet_readback_nats(ctx, ids, len(net_ids), vals, ints))
     none = (1 << 64) - 1
     return [None if v == none else v for v in vals[:len(net_ids)]], list(ints[:len(net_ids)])
+
+
+def inet_readback_nats_begin(ctx, net_ids) -> None:
+    ids = (C.c_int32 * max(1, len(net_ids)))(*net_ids)
+    _check(ctx, LIB.inet_readback_nats_begin(ctx, ids, len(net_ids)))
+
+
+def readback_buffers():
+    """Output arrays for inet_readback_nats_end (one pair per context)."""
+    return (C.c_uint64 * READ_CHUNK)(), (C.c_uint64 * READ_CHUNK)()
+
+
+def inet_readback_nats_end(ctx, wait: bool, bufs=None):
+    """(values, interactions) of the batch begun last, or None while it runs."""
+    vals, ints = bufs if bufs is not None else readback_buffers()
+    n = C.c_int32()
+    _check(ctx, LIB.inet_readback_nats_end(ctx, 1 if wait else 0, vals, ints, READ_CHUNK, C.byref(n)))
+    if n.value < 0:
+        return None
+    none = (1 << 64) - 1
+    return [None if v == none else v for v in vals[:n.value]], list(ints[:n.value])
 
 
 def inet_trace(ctx) -> tuple[list[int], list[int]]:

@@ -132,6 +132,13 @@ struct inet_ctx {
   std::vector<long long> tr_front, tr_live;
   bool poisoned = false;
   uint64_t h2d_bytes = 0, d2h_bytes = 0;  // host<->device bytes copied by this context
+  // non-blocking numeral readback: one batch at a time on a second stream
+  cudaStream_t rb_stream = nullptr;
+  cudaEvent_t rb_ready = nullptr, rb_after = nullptr;
+  uint32_t* rb_host_roots = nullptr;       // pinned, kReadChunk entries
+  unsigned long long* rb_host_vals = nullptr;
+  std::vector<uint64_t> rb_inter;           // interactions of the batch in flight
+  int32_t rb_n = -1;                        // nets of the batch in flight, -1: none
   std::string err;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -473,6 +480,14 @@ void inet_destroy(inet_ctx* ctx) {
   if (!ctx->host_only) {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->rb_stream) {
+      cudaStreamSynchronize(ctx->rb_stream);
+      cudaStreamDestroy(ctx->rb_stream);
+    }
+    if (ctx->rb_ready) cudaEventDestroy(ctx->rb_ready);
+    if (ctx->rb_after) cudaEventDestroy(ctx->rb_after);
+    if (ctx->rb_host_roots) cudaFreeHost(ctx->rb_host_roots);
+    if (ctx->rb_host_vals) cudaFreeHost(ctx->rb_host_vals);
     drop_graph(ctx);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -857,6 +872,7 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
                                uint64_t* interactions_out) {
   if (!ctx || n < 0 || (n > 0 && (!net_ids || !values_out))) return INET_ERR_INVALID_ARG;
   if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (ctx->rb_n >= 0) return fail(ctx, INET_ERR_STATE, "a non-blocking readback is in flight");
   if (n == 0) return INET_OK;
   std::vector<uint32_t> roots((size_t)n);
   for (int32_t i = 0; i < n; i++) {
@@ -887,6 +903,81 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
     CK(d2h(ctx, values_out + off, dval, sizeof(unsigned long long) * (size_t)m));
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  return INET_OK;
+}
+
+inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
+  if (!ctx || n < 0 || (uint32_t)n > kReadChunk || (n > 0 && !net_ids)) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  if (ctx->rb_n >= 0) return fail(ctx, INET_ERR_STATE, "a non-blocking readback is already in flight");
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  if ((s = upload_staged(ctx))) return s;
+  if (!ctx->rb_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->rb_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->rb_ready, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->rb_after, cudaEventDisableTiming));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->rb_host_roots), sizeof(uint32_t) * kReadChunk, 0));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->rb_host_vals), sizeof(unsigned long long) * kReadChunk, 0));
+  }
+  ctx->rb_inter.assign((size_t)n, 0);
+  for (int32_t i = 0; i < n; i++) {
+    if ((s = check_net(ctx, net_ids[i]))) return s;
+    const NetRec& nr = ctx->nets[(size_t)net_ids[i]];
+    ctx->rb_host_roots[i] = nr.iface.size() == 1 ? nr.iface[0] : kEmpty;
+    ctx->rb_inter[(size_t)i] = ctx->h_netctr[(size_t)net_ids[i]] & kNetIntMask;
+  }
+  auto si = ctx->rules.index.find("S");
+  auto zi = ctx->rules.index.find("Z");
+  if (si == ctx->rules.index.end() || zi == ctx->rules.index.end()) {
+    for (int32_t i = 0; i < n; i++) ctx->rb_host_vals[i] = ~0ull;
+    CK(cudaEventRecord(ctx->rb_ready, ctx->rb_stream));
+  } else if (n > 0) {
+    // after everything queued on the main stream so far (the reduction that
+    // finished these nets); later reductions of other nets run alongside
+    uint32_t* droot = at<uint32_t>(ctx, ctx->lay.rb_root);
+    unsigned long long* dval = at<unsigned long long>(ctx, ctx->lay.rb_val);
+    CK(cudaEventRecord(ctx->rb_after, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->rb_stream, ctx->rb_after, 0));
+    CK(cudaMemcpyAsync(droot, ctx->rb_host_roots, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                       ctx->rb_stream));
+    k_read_nats<<<(n + 255) / 256, 256, 0, ctx->rb_stream>>>(ctx->dev, droot, (uint32_t)n, si->second, zi->second,
+                                                             dval);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->rb_host_vals, dval, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToHost,
+                       ctx->rb_stream));
+    CK(cudaEventRecord(ctx->rb_ready, ctx->rb_stream));
+    ctx->h2d_bytes += sizeof(uint32_t) * (size_t)n;
+    ctx->d2h_bytes += sizeof(unsigned long long) * (size_t)n;
+  } else {
+    CK(cudaEventRecord(ctx->rb_ready, ctx->rb_stream));
+  }
+  ctx->rb_n = n;
+  return INET_OK;
+}
+
+inet_status inet_readback_nats_end(inet_ctx* ctx, int32_t wait, uint64_t* values_out, uint64_t* interactions_out,
+                                   int32_t cap, int32_t* n_out) {
+  if (!ctx || !n_out || cap < 0 || (cap > 0 && !values_out)) return INET_ERR_INVALID_ARG;
+  *n_out = -1;
+  if (ctx->rb_n < 0) return fail(ctx, INET_ERR_STATE, "no non-blocking readback in flight");
+  if (cap < ctx->rb_n) return fail(ctx, INET_ERR_INVALID_ARG, "output arrays shorter than the batch");
+  DeviceGuard g(ctx->device);
+  if (wait) {
+    CK(cudaEventSynchronize(ctx->rb_ready));
+  } else {
+    const cudaError_t e = cudaEventQuery(ctx->rb_ready);
+    if (e == cudaErrorNotReady) return INET_OK;
+    CK(e);
+  }
+  for (int32_t i = 0; i < ctx->rb_n; i++) {
+    values_out[i] = ctx->rb_host_vals[i];
+    if (interactions_out) interactions_out[i] = ctx->rb_inter[(size_t)i];
+  }
+  *n_out = ctx->rb_n;
+  ctx->rb_n = -1;
   return INET_OK;
 }
 
@@ -928,6 +1019,12 @@ inet_status inet_trace(inet_ctx* ctx, int64_t* frontier, int64_t* live, size_t c
 
 inet_status inet_reset(inet_ctx* ctx) {
   if (!ctx) return INET_ERR_INVALID_ARG;
+  if (ctx->rb_n >= 0) {
+    // a readback still walks this arena: let it end, drop its results
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->rb_stream);
+    ctx->rb_n = -1;
+  }
   ctx->nets.clear();
   ctx->h_netctr.clear();
   ctx->h_netstat.clear();

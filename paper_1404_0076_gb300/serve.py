@@ -4,8 +4,10 @@ Requests (one net each) are admitted as they arrive, while the arena they go
 to has room for them by an estimate of their footprint; every admitted net
 joins the frontier of the nets already in flight (inet_stage), and the
 device runs the asynchronous loop in bounded epochs (slice_us), between
-which finished nets are harvested (inet_net_pending, inet_readback_nats)
-and new ones admitted.  Requests therefore overlap on the device with
+which finished nets are found (inet_net_pending) and new ones admitted.
+The results of finished nets are read back on a second stream
+(inet_readback_nats_begin / _end) while the device keeps reducing the
+others, so a long readback walk never stalls the loop.  Requests therefore overlap on the device with
 whatever is in flight; each result is independent of the mix because nets
 share no agent and interactions are local (Sec. 2.1).
 
@@ -38,21 +40,12 @@ class Finished:
         return self.finished - self.arrival
 
 
-def agents_in(text: str) -> int:
-    """Agent symbols in a net's text (upper-case initials)."""
-    n = 0
-    prev = " "
-    for ch in text:
-        if ch.isupper() and not (prev.isalnum() or prev == "_"):
-            n += 1
-        prev = ch
-    return n
-
-
 def default_footprint(text: str, size: int) -> int:
-    """Estimated peak agent slots of a request: its agents plus a share per
-    expected interaction (numerals built by the net stay alive)."""
-    return 2 * agents_in(text) + size + 64
+    """Estimated peak agent slots of a request, without scanning its text:
+    every agent symbol takes at least two characters of the text ("S(",
+    "Z,"), so len(text) is at least twice the net's agents; plus a share
+    per expected interaction (numerals built by the net stay alive)."""
+    return len(text) + size + 64
 
 
 class Server:
@@ -83,6 +76,9 @@ class Server:
         self.nets = [0, 0]          # nets loaded per arena since its reset
         self.inflight = [{}, {}]    # arena -> {net id: (rid, arrival, admitted)}
         self.unstaged = [[], []]    # admitted nets not yet handed to the device
+        self.done_nets = [set(), set()]  # finished, waiting for or in a readback
+        self.ready = [[], []]       # finished, readback not yet begun
+        self.rb_batch = [None, None]  # nets of the readback in flight
         self.epochs = 0
         self.switches = 0
 
@@ -99,6 +95,9 @@ class Server:
         self.used[k] = 0
         self.nets[k] = 0
         self.unstaged[k] = []
+        self.done_nets[k] = set()
+        self.ready[k] = []
+        self.rb_batch[k] = None
 
     def try_admit(self, rid: int, text: str, size: int, arrival: float, now: float) -> bool:
         need = self.footprint(text, size)
@@ -123,33 +122,54 @@ class Server:
     # -- device epochs and harvest ------------------------------------------
     def epoch(self, now_fn) -> list[Finished]:
         done = []
+        reduced = False
         for k in (0, 1):
+            ev = self.ctx[k]
             if self.unstaged[k]:
-                self.ctx[k].stage(self.unstaged[k])   # one upload for every net admitted since
+                ev.stage(self.unstaged[k])   # one upload for every net admitted since
                 self.unstaged[k] = []
-            if not self.inflight[k]:
-                continue
-            st = self.ctx[k].reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
-                                    check=False)
-            self.epochs += 1
-            ids = list(self.inflight[k].keys())
-            if st["status"] not in ("OK", "STEP_LIMIT", "NO_RULE"):
-                # a fatal error poisons the arena: every request in it fails
-                t = now_fn()
-                for nid in ids:
-                    rid, arr, adm = self.inflight[k].pop(nid)
-                    done.append(Finished(rid, arr, adm, t, None, 0, st["status"]))
-                self._reset(k)
-                continue
-            pend = self.ctx[k].pending(ids)
-            fin = [nid for nid, p in zip(ids, pend) if p == 0]
-            if fin:
-                vals, ints = self.ctx[k].readback_nats(fin)
-                t = now_fn()
-                for nid, v, n in zip(fin, vals, ints):
-                    rid, arr, adm = self.inflight[k].pop(nid)
-                    done.append(Finished(rid, arr, adm, t, v, n))
+            running = [nid for nid in self.inflight[k] if nid not in self.done_nets[k]]
+            if running:
+                st = ev.reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
+                               check=False)
+                self.epochs += 1
+                reduced = True
+                if st["status"] not in ("OK", "STEP_LIMIT", "NO_RULE"):
+                    # a fatal error poisons the arena: every request in it fails
+                    t = now_fn()
+                    for nid in list(self.inflight[k]):
+                        rid, arr, adm = self.inflight[k].pop(nid)
+                        done.append(Finished(rid, arr, adm, t, None, 0, st["status"]))
+                    self._reset(k)
+                    continue
+                fin = [nid for nid, p in zip(running, ev.pending(running)) if p == 0]
+                self.ready[k].extend(fin)
+                self.done_nets[k].update(fin)
+            done.extend(self._harvest(k, now_fn, wait=False))
+        if not reduced and any(b is not None for b in self.rb_batch):
+            time.sleep(50e-6)   # only readbacks in flight: poll gently
         return done
+
+    def _harvest(self, k: int, now_fn, wait: bool) -> list[Finished]:
+        """Completes the readback in flight (if done) and begins the next."""
+        out = []
+        ev = self.ctx[k]
+        if self.rb_batch[k] is not None:
+            r = ev.readback_nats_end(wait)
+            if r is None:
+                return out
+            vals, ints = r
+            t = now_fn()
+            for nid, v, n in zip(self.rb_batch[k], vals, ints):
+                rid, arr, adm = self.inflight[k].pop(nid)
+                self.done_nets[k].discard(nid)
+                out.append(Finished(rid, arr, adm, t, v, n))
+            self.rb_batch[k] = None
+        if self.ready[k]:
+            batch, self.ready[k] = self.ready[k][:65536], self.ready[k][65536:]
+            ev.readback_nats_begin(batch)
+            self.rb_batch[k] = batch
+        return out
 
     def busy(self) -> bool:
         return bool(self.inflight[0] or self.inflight[1])

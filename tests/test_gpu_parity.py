@@ -421,3 +421,40 @@ def test_batched_nat_readback_leaves_the_trace(orc):
     assert ev.readback_nats(ids)[0] == [25, 42]
     assert ev.trace() == tr
     ev.close()
+
+
+def test_nonblocking_readback_overlaps_reduction(orc):
+    # finished nets are read back on the context's second stream while the
+    # main stream keeps reducing another net of the same arena
+    from paper_1404_0076_gb300.capi import InetError
+    first = [W.add_net(3000, 7), W.mul_net(40, 30), W.fib_net(14), "< a, b | Add(a, b) = Z >"]
+    o = orc.run(R, first)
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(first)
+    ev.reduce(ids, mode="async")
+    with pytest.raises(InetError):
+        ev.readback_nats_end()              # nothing begun
+    ev.readback_nats_begin(ids)
+    with pytest.raises(InetError):
+        ev.readback_nats_begin(ids)         # one batch at a time
+    with pytest.raises(InetError):
+        ev.readback_nats(ids)               # the blocking form shares its scratch
+    late = ev.load_net(W.ack_net(3, 5))
+    ev.reduce([late], mode="async")
+    r = None
+    for _ in range(100000):
+        r = ev.readback_nats_end()
+        if r is not None:
+            break
+    assert r is not None
+    vals, ints = r
+    assert vals == [x["nat"] for x in o] and ints == [x["interactions"] for x in o]
+    assert ev.readback_nat(late)[0] == 253
+    ev.readback_nats_begin([late])
+    assert ev.readback_nats_end(wait=True) == ([253], [ev.net_info(late)["interactions"]])
+    ev.readback_nats_begin(ids)
+    ev.reset()                              # waits for the walk, drops it
+    with pytest.raises(InetError):
+        ev.readback_nats_end()
+    ev.close()

@@ -29,6 +29,7 @@ class FakeEvaluator:
         self.next_id = 0
         self.resets = 0
         self.staged = set()
+        self.batch = None
 
     def load_rules(self, text):
         pass
@@ -56,12 +57,28 @@ class FakeEvaluator:
     def readback_nats(self, ids):
         return [self.value[i] for i in ids], [self.value[i] // 10 for i in ids]
 
+    def readback_nats_begin(self, ids):
+        assert self.batch is None
+        assert all(self.left[i] == 0 for i in ids)
+        self.batch = list(ids)
+        self.polls = 0
+
+    def readback_nats_end(self, wait=False):
+        assert self.batch is not None
+        self.polls += 1
+        if not wait and self.polls < 2:   # done at the second poll
+            return None
+        r = self.readback_nats(self.batch)
+        self.batch = None
+        return r
+
     def reset(self):
         self.resets += 1
         self.left.clear()
         self.value.clear()
         self.staged.clear()
         self.next_id = 0
+        self.batch = None
 
     def close(self):
         pass
