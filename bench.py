@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
+from paper_1404_0076_gb300.shard import combine, rank_seed  # noqa: E402
 
 METRIC = "interactions/sec and HBM-roofline fraction (batched vs plain); p50/p99 latency"
 UNIT = "interactions/s"
@@ -39,11 +40,11 @@ def workload(name: str, rank: int = 0):
     """(nets, description, capacities) of a named workload.  Under N ranks
     each rank reduces its own batch (seed offset by rank): weak scaling."""
     if name == "mul2048":
-        w = W.config1(seed=W.SEED_BASE + 1 + 1000 * rank)
+        w = W.config1(seed=rank_seed(W.SEED_BASE + 1, rank))
         desc = "2048 nets Mul(S^m Z, S^n Z), m,n ~ U{0..64}, seed 14040076+1"
         caps = dict(max_agents=1 << 24, max_vars=1 << 24, max_pairs=1 << 20, max_nets=4096)
     elif name == "add4096":
-        w = W.config0(seed=W.SEED_BASE + 0 + 1000 * rank)
+        w = W.config0(seed=rank_seed(W.SEED_BASE + 0, rank))
         desc = "4096 nets Add(S^m Z, S^n Z), m,n ~ U{0..256}, seed 14040076"
         caps = dict(max_agents=1 << 22, max_vars=1 << 22, max_pairs=1 << 20, max_nets=8192)
     elif name == "ack3":
@@ -219,38 +220,52 @@ def expected_value(r) -> int:
 
 def serving_leg(args, local: int) -> dict:
     """Continuous batching on the serving mix: the first --serve-requests
-    requests of the 100k-request Poisson stream (1000 requests/s), replayed
-    on the wall clock, then the same requests all at once (saturated).
-    Every result is checked against its closed form (value and exact
-    interaction count)."""
+    requests of the 100k-request Poisson stream.  First all at once
+    (saturated), which measures the serving capacity C in interactions/s;
+    then replayed on the wall clock at load rho of C (arrival rate
+    rho * C / mean request size) for rho in 0.5, 0.8, 0.95, and at the
+    stream's own 1000 requests/s.  Every result is checked against its
+    closed form (value and exact interaction count)."""
     import dataclasses
 
     from paper_1404_0076_gb300.serve import Server, summarize
     reqs = W.config4()[: args.serve_requests]
     expect = [expected_value(r) for r in reqs]
+    mean_size = sum(r.size for r in reqs) / len(reqs)
     budget = args.serve_budget_gb << 30
     srv = Server(W.ARITH_RULES, device=local, budget_bytes=budget, epoch_us=args.serve_epoch_us, max_pairs=1 << 23)
-    out = {"workload": "serving mix: Poisson arrivals at 1000 requests/s, one net each from add/mul/ack/fib, "
-                       "sizes lognormal (median 1e3 interactions, sigma 2.16, clipped to 1e7), seed 14040076+4",
-           "requests": len(reqs), "budget_bytes": budget, "arenas": 2, "epoch_us": args.serve_epoch_us,
-           "sample": f"first {len(reqs)} of the 100000-request stream"}
+    out = {"workload": "serving mix: Poisson arrivals, one net each from add/mul/ack/fib, sizes lognormal "
+                       "(median 1e3 interactions, sigma 2.16, clipped to 1e7), seed 14040076+4",
+           "requests": len(reqs), "mean_request_interactions": mean_size, "budget_bytes": budget, "arenas": 2,
+           "epoch_us": args.serve_epoch_us, "sample": f"first {len(reqs)} of the 100000-request stream"}
+
+    def run(scale: float) -> dict:
+        e0, s0 = srv.epochs, srv.switches
+        t0 = time.perf_counter()
+        done = srv.serve(reqs, time_scale=scale)
+        wall = time.perf_counter() - t0
+        rec = summarize(done, wall)
+        rec.update(wall_s=wall, epochs=srv.epochs - e0, arena_switches=srv.switches - s0,
+                   wrong=sum(1 for d in done if d.status != "OK"
+                             or (d.value, d.interactions) != (expect[d.rid], reqs[d.rid].size)))
+        return rec
+
     try:
         srv.serve([dataclasses.replace(r, arrival_s=0.0) for r in reqs[:64]])  # warm-up
-        for name, scale in (("poisson", 1.0), ("saturated", 0.0)):
-            e0, s0 = srv.epochs, srv.switches
-            t0 = time.perf_counter()
-            done = srv.serve(reqs, time_scale=scale)
-            wall = time.perf_counter() - t0
-            rec = summarize(done, wall)
-            rec["wall_s"] = wall
-            rec["epochs"] = srv.epochs - e0
-            rec["arena_switches"] = srv.switches - s0
-            rec["wrong"] = sum(1 for d in done if d.status != "OK"
-                               or (d.value, d.interactions) != (expect[d.rid], reqs[d.rid].size))
-            out[name] = rec
+        out["saturated"] = run(0.0)
+        cap = out["saturated"]["interactions_per_s"]
+        out["capacity_interactions_per_s"] = cap
+        rate0 = len(reqs) / reqs[-1].arrival_s          # the stream's own rate
+        for rho in (0.5, 0.8, 0.95):
+            lam = rho * cap / mean_size                   # requests per second
+            rec = run(rate0 / lam)
+            rec["rho"], rec["requests_per_s"] = rho, lam
+            out[f"rho_{rho}"] = rec
+        rec = run(1.0)
+        rec["requests_per_s"] = rate0
+        out["stream_rate"] = rec
     finally:
         srv.close()
-    out["offered_interactions_per_s"] = sum(r.size for r in reqs) / max(1e-9, reqs[-1].arrival_s)
     return out
 
 
@@ -270,7 +285,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--serve-requests", type=int, default=6000)
     ap.add_argument("--serve-epoch-us", type=int, default=250)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     args = ap.parse_args()
@@ -297,6 +313,14 @@ def main():
     bpr = bytes_per_rule(rules, batched=len(nets) > 1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 129 MB L2
     opts = dict(mode=args.mode, block=args.block, grid=args.grid, solo_max=args.solo_max)
+    tuned = None
+    if not args.no_tune and not (args.block or args.grid or args.solo_max):
+        # launch shape from the autotuner (timed runs outside the measured steps)
+        from paper_1404_0076_gb300.autotune import Autotuner
+        props = torch.cuda.get_device_properties(local)
+        tuned = Autotuner().tune(
+            ev, W.ARITH_RULES, nets, args.mode, gpu=props.name, num_sms=props.multi_processor_count)
+        opts.update(tuned)
 
     def prepared():
         ev.reset()
@@ -322,15 +346,10 @@ def main():
             launches += st["launches"]
             alg_bytes += sum(c * b for c, b in zip(st["per_rule"], bpr))
     torch.cuda.synchronize()
-    total_s = sum(dev_ms) / 1e3
     if dist:
-        t = torch.tensor([total_s, float(ints)], dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_s_max, ints_all = float(tmax[0]), float(t[1])
-    else:
-        total_s_max, ints_all = total_s, float(ints)
+        dist.barrier()
+    total_s = sum(dev_ms) / 1e3
+    total_s_max, ints_all = combine(total_s, ints, dist)
     value = ints_all / total_s_max
 
     # roofline of the dominant kernel: one launch of it per step (k_async or
@@ -343,6 +362,30 @@ def main():
             "kernel": {"async": "k_async", "persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[args.mode],
             "launch_time": "device time of the reduce call (for async: the queue fill, set-up and wind-down "
                            "kernels around k_async add a few microseconds)"}
+
+    # secondary bounds.  Atomic units: every equation linked is at most one
+    # exchange on a name slot; measured random exchanges per second, in a
+    # slot array that fits L2 and in one that does not.  Critical path: the
+    # number of maximally parallel steps (the persistent form's step count)
+    # times the time per interaction along one dependency chain.
+    from paper_1404_0076_gb300 import capi
+    links = [r["n_link"] for r in rules]
+    hist_tot = st["per_rule"]
+    exch_per_int = sum(c * l for c, l in zip(hist_tot, links)) / max(1, sum(hist_tot))
+    ex_l2 = capi.inet_bench_exch(local, 1 << 22, 1 << 28)
+    ex_hbm = capi.inet_bench_exch(local, 1 << 30, 1 << 28)
+    roof["atomics"] = {"exch_per_s_l2_resident": ex_l2, "exch_per_s_hbm": ex_hbm,
+                       "exch_per_interaction_max": exch_per_int,
+                       "interactions_per_s_bound": ex_hbm / max(1e-9, exch_per_int),
+                       "frac": value / (ex_hbm / max(1e-9, exch_per_int)),
+                       "how": "inet_bench_exch: random 32-bit atomicExch returning the old value, 16 MiB and 4 GiB arrays"}
+    prepared()
+    stp_depth = ev.reduce([], mode="persistent")
+    depth = stp_depth["steps"]
+    roof["critical_path"] = {"depth_steps": depth,
+                             "ns_per_level": 1e9 * (total_s / args.steps) / max(1, depth),
+                             "how": "depth = steps of the maximally parallel loop (persistent form) on the same batch; "
+                                    "ns_per_level = timed device time per step / depth"}
 
     # e2e: public API from host text to host results, copies included
     e2e_ms, e2e_h2d, e2e_d2h, e2e_int = [], 0, 0, 0
@@ -405,7 +448,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": desc, "nets_per_rank": len(nets), "interactions_per_step": ints // args.steps,
-                           "mode": args.mode, "block": args.block or 256, "grid": args.grid or "auto",
+                           "mode": args.mode, "block": opts["block"] or 256, "grid": opts["grid"] or "auto",
+                           "launch_shape": "autotuned" if tuned else "given",
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"independent batches, {world} rank(s)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -249,6 +249,14 @@ inet_status inet_trace(inet_ctx* ctx, int64_t* frontier, int64_t* live, size_t c
  * Clears a poisoned state. */
 inet_status inet_reset(inet_ctx* ctx);
 
+/* Microbenchmark of the linker's primitive (->com, Sec. 2.2): random 32-bit
+ * atomic exchanges that return the old value, over an array of n_slots
+ * slots (allocated and freed here) on CUDA device `device`; about n_ops
+ * exchanges are timed after one warm-up launch.  *exch_per_s_out gets
+ * exchanges per second.  It gives the atomic-throughput bound on the
+ * interaction rate beside the HBM roofline. */
+inet_status inet_bench_exch(int device, uint64_t n_slots, uint64_t n_ops, double* exch_per_s_out);
+
 /* ---- Reduction without any allocation ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate on their request path: a serving process whose allocator

@@ -41,7 +41,7 @@ EXPORTED = [
     "inet_load_rules", "inet_rule_count", "inet_rule_info", "inet_load_net", "inet_reduce",
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
-    "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end",
+    "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -108,6 +108,7 @@ def _load():
         "inet_readback_nats": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64),
                                 C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats_begin": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
+        "inet_bench_exch": ([C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_double)], C.c_int32),
         "inet_readback_nats_end": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int32,
                                     C.POINTER(C.c_int32)], C.c_int32),
         "inet_trace": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_size_t, C.POINTER(C.c_size_t)],
@@ -254,6 +255,15 @@ def inet_readback_nats(ctx, net_ids) -> tuple[list[int | None], list[int]]:
 def inet_readback_nats_begin(ctx, net_ids) -> None:
     ids = (C.c_int32 * max(1, len(net_ids)))(*net_ids)
     _check(ctx, LIB.inet_readback_nats_begin(ctx, ids, len(net_ids)))
+
+
+def inet_bench_exch(device: int, n_slots: int, n_ops: int) -> float:
+    """Random atomic exchanges per second over n_slots 32-bit slots."""
+    out = C.c_double()
+    st = LIB.inet_bench_exch(device, n_slots, n_ops, C.byref(out))
+    if st != INET_OK:
+        raise InetError(st, "inet_bench_exch failed")
+    return out.value
 
 
 def readback_buffers():

@@ -13,6 +13,7 @@
 #include "inet.h"
 #include "inet_async.cuh"
 #include "inet_kernels.cuh"
+#include "inet_micro.cuh"
 #include "inet_text.h"
 
 using namespace inet;
@@ -1044,6 +1045,42 @@ inet_status inet_reset(inet_ctx* ctx) {
   if (ctx->host_only || !ctx->ws_ready) return INET_OK;
   DeviceGuard g(ctx->device);
   return clear_device(ctx);
+}
+
+inet_status inet_bench_exch(int device, uint64_t n_slots, uint64_t n_ops, double* exch_per_s_out) {
+  if (!exch_per_s_out || n_slots == 0 || n_ops == 0) return INET_ERR_INVALID_ARG;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return INET_ERR_NO_DEVICE;
+  DeviceGuard g(device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return INET_ERR_CUDA;
+  const uint32_t block = 256, grid = (uint32_t)sms * 8;
+  const uint64_t threads = (uint64_t)block * grid;
+  const uint32_t per = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(n_ops / threads, 1u << 20));
+  uint32_t* slots = nullptr;
+  unsigned long long* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  inet_status st = INET_OK;
+  float ms = 0;
+  if (cudaMalloc(&slots, n_slots * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&sink, 8) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = INET_ERR_CUDA;
+  } else {
+    cudaMemset(slots, 0, n_slots * sizeof(uint32_t));
+    cudaMemset(sink, 0, 8);
+    k_bench_exch<<<grid, block>>>(slots, n_slots, per, 1, sink);  // warm-up
+    cudaEventRecord(e0);
+    k_bench_exch<<<grid, block>>>(slots, n_slots, per, 2, sink);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = INET_ERR_CUDA;
+    else cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (st == INET_OK) *exch_per_s_out = ms > 0 ? (double)threads * per / (ms * 1e-3) : 0.0;
+  if (slots) cudaFree(slots);
+  if (sink) cudaFree(sink);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
 }
 
 const char* inet_last_error(const inet_ctx* ctx) {

@@ -1,0 +1,33 @@
+// Microbenchmark of the linker's memory primitive: 32-bit atomic exchanges
+// that return the old value (->com on a name slot, Sec. 2.2), at random
+// slots of an array of a given size.  It bounds the interaction rate from
+// the side of the L2 atomic units, beside the HBM roofline: an interaction
+// links a handful of equations, each one such exchange.
+#pragma once
+
+#include <cstdint>
+
+namespace inet {
+
+// splitmix64 (Steele, Lea and Flood, 2014): a counter-based mixer of a
+// 64-bit state, here the address stream of each thread.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_bench_exch(uint32_t* slots, uint64_t n_slots, uint32_t ops_per_thread, uint64_t seed,
+                             unsigned long long* sink) {
+  uint64_t s = seed + (uint64_t)(blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * 0x2545F4914F6CDD1Dull;
+  uint32_t acc = 0;
+  for (uint32_t i = 0; i < ops_per_thread; i++) {
+    const uint64_t r = splitmix64(s);
+    const uint64_t idx = __umul64hi(r, n_slots);  // uniform in [0, n_slots)
+    acc ^= atomicExch(slots + idx, (uint32_t)r);
+  }
+  if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);  // keeps the returned values live
+}
+
+}  // namespace inet

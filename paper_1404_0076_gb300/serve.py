@@ -204,16 +204,27 @@ class Server:
         return out
 
 
-def summarize(done: list[Finished], wall_s: float) -> dict:
-    lat = sorted(f.latency for f in done)
+def _pct(xs: list[float], p: float):
+    """The p-th percentile (nearest rank) of sorted xs, or None."""
+    if not xs:
+        return None
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(p / 100.0 * len(xs))) - 1))]
 
-    def pct(p):
-        if not lat:
-            return None
-        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+
+def summarize(done: list[Finished], wall_s: float) -> dict:
+    """Latency percentiles (arrival to result on the host), split into the
+    wait for admission and the time from admission to result."""
+    lat = sorted(f.latency for f in done)
+    wait = sorted(f.admitted - f.arrival for f in done)
+    serv = sorted(f.finished - f.admitted for f in done)
+
+    def ms(x):
+        return None if x is None else 1e3 * x
 
     ints = sum(f.interactions for f in done)
-    return {"requests": len(done), "p50_ms": 1e3 * pct(50) if lat else None, "p99_ms": 1e3 * pct(99) if lat else None,
-            "mean_ms": 1e3 * sum(lat) / len(lat) if lat else None, "interactions": ints,
-            "interactions_per_s": ints / wall_s if wall_s > 0 else None,
+    return {"requests": len(done), "p50_ms": ms(_pct(lat, 50)), "p99_ms": ms(_pct(lat, 99)),
+            "mean_ms": ms(sum(lat) / len(lat)) if lat else None,
+            "admission_wait_p50_ms": ms(_pct(wait, 50)), "admission_wait_p99_ms": ms(_pct(wait, 99)),
+            "service_p50_ms": ms(_pct(serv, 50)), "service_p99_ms": ms(_pct(serv, 99)),
+            "interactions": ints, "interactions_per_s": ints / wall_s if wall_s > 0 else None,
             "failed": sum(1 for f in done if f.status != "OK")}

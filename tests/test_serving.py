@@ -165,3 +165,14 @@ def test_results_in_the_mix_equal_results_alone(oracle):
     # another one was still in flight
     spans = sorted((d.admitted, d.finished) for d in done)
     assert any(b[0] < a[1] for a, b in zip(spans, spans[1:]))
+
+
+def test_summary_percentiles_on_cpu():
+    from paper_1404_0076_gb300.serve import Finished
+    done = [Finished(i, 0.0, 0.001 * i, 0.01 * (i + 1), i, i) for i in range(100)]
+    s = summarize(done, 2.0)
+    assert s["p50_ms"] == 500.0 and s["p99_ms"] == 990.0
+    assert s["admission_wait_p50_ms"] == 49.0
+    assert abs(s["service_p50_ms"] - 451.0) < 1e-9
+    assert s["interactions_per_s"] == sum(range(100)) / 2.0
+    assert summarize([], 1.0)["p50_ms"] is None
