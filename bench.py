@@ -55,6 +55,10 @@ def workload(name: str, rank: int = 0):
         w = W.config3()
         desc = "6 nets Fib(S^n Z), n = 20..25"
         caps = dict(max_agents=1 << 23, max_vars=1 << 23, max_pairs=1 << 20, max_nets=64)
+    elif name == "chain20k":
+        w = W.Workload("chain20k", W.ARITH_RULES, [W.add_net(20000, 0)], [(20000, 0)])
+        desc = "one net Add(Z, r) = S^20000 Z: a chain of 20001 dependent interactions"
+        caps = dict(max_agents=1 << 20, max_vars=1 << 20, max_pairs=1 << 16, max_nets=16)
     elif name == "fib25x64":
         w = W.replicated(W.config3(ns=(25,)), 64)
         desc = "64 copies of Fib(S^25 Z)"

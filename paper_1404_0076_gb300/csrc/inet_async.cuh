@@ -37,8 +37,7 @@ struct WarpMem {
   uint32_t astk[kAStack];
   uint32_t vstk[kVStack];
   uint32_t vstage[kVStageW];
-  unsigned long long bc[10];  // lane-0 broadcasts
-  int acount, vcount, vstage_n, pad;
+  int vstage_n, pad[3];
 };
 
 __host__ __device__ inline size_t async_smem_bytes(uint32_t block, uint32_t n_labels, uint32_t n_tmpl) {
@@ -103,24 +102,46 @@ __device__ __forceinline__ bool link_async(const Dev& d, WarpMem& W, uint32_t t,
   }
 }
 
-__device__ __forceinline__ unsigned long long warp_excl_scan64(unsigned long long v, unsigned long long* total) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(kFull, inc, o);
-    if (lane >= o) inc += t;
-  }
-  *total = __shfl_sync(kFull, inc, 31);
-  return inc - v;
+// Rule template as the asynchronous kernel reads it from shared memory: one
+// 32-bit word per new agent (label and its three port codes) and one 16-bit
+// word per equation, so an agent or an equation costs one load.
+struct AsyncTpl {
+  uint32_t hdr;                 // n_new | n_fresh << 8 | n_link << 16 | rule << 24
+  uint32_t agent[kMaxNew];      // lab | src0 << 8 | src1 << 16 | src2 << 24
+  uint16_t link[kMaxLink];      // code0 | code1 << 8
+  uint32_t pad[3];
+};
+static_assert(sizeof(AsyncTpl) == 64, "packed template is 64 bytes");
+
+__device__ __forceinline__ AsyncTpl pack_template(const Template& t) {
+  AsyncTpl p;
+  p.hdr = (uint32_t)t.n_new | ((uint32_t)t.n_fresh << 8) | ((uint32_t)t.n_link << 16) | ((uint32_t)t.rule << 24);
+  for (int j = 0; j < kMaxNew; j++)
+    p.agent[j] = (uint32_t)t.lab[j] | ((uint32_t)t.src[j][0] << 8) | ((uint32_t)t.src[j][1] << 16) |
+                 ((uint32_t)t.src[j][2] << 24);
+  for (int k = 0; k < kMaxLink; k++) p.link[k] = (uint16_t)(t.link[k][0] | (t.link[k][1] << 8));
+  p.pad[0] = p.pad[1] = p.pad[2] = 0;
+  return p;
 }
+
+// Port value of code c (0xFF: none) from the lane's value table.
+__device__ __forceinline__ int32_t port_val(const WarpMem& W, uint32_t c, int lane) {
+  return c == kValNone ? 0 : (int32_t)W.vals[c][lane];
+}
+
+// Free slots this warp holds privately: warp-uniform counts, kept in the
+// registers of every lane.
+struct WarpStacks {
+  int ac, vc;
+};
 
 // One interaction per lane whose `valid` is set (warp-collective).  The new
 // active pairs are left in W.out[0..return)[lane]; a pair that cannot be
 // reduced (no rule, corrupt state) is dropped and returns 0.  Lane 0's
 // `live` collects the change of live agents.
-__device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int16_t* tab, uint32_t* hist,
-                                   WarpMem& W, bool valid, uint32_t a, uint32_t b, long long& live) {
+__device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl* tmpl, const int16_t* tab,
+                                                   uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
+                                                   uint32_t a, uint32_t b, long long& live) {
   const int lane = threadIdx.x & 31;
   Ctrl* c = d.ctrl;
   uint32_t net = 0, ti = 0;
@@ -133,7 +154,7 @@ __device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int
     ra = ld_node(d.node + a);
     rb = ld_node(d.node + b);
     const uint32_t la = (uint32_t)ra.x & 0xFFu, lb = (uint32_t)rb.x & 0xFFu;
-    int e = (la < d.n_labels && lb < d.n_labels) ? tab[la * d.n_labels + lb] : -1;
+    const int e = (la < d.n_labels && lb < d.n_labels) ? tab[la * d.n_labels + lb] : -1;
     net = (uint32_t)ra.x >> 8;
     if (net >= d.max_nets) {
       set_error(c, INET_ERR_STATE, 3);
@@ -151,57 +172,48 @@ __device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int
       ti = (uint32_t)e >> 1;
     }
   }
-  const Template& T = tmpl[ti];
-  const uint32_t n_new = valid ? T.n_new : 0u;
-  const uint32_t n_fresh = valid ? T.n_fresh : 0u;
+  const AsyncTpl& T = tmpl[ti];
+  const uint32_t hdr = valid ? T.hdr : 0u;
+  const uint32_t n_new = hdr & 0xFFu, n_fresh = (hdr >> 8) & 0xFFu, n_link = (hdr >> 16) & 0xFFu;
   const uint32_t need_a = n_new > 2 ? n_new - 2 : 0u;
   const uint32_t free_a = valid && n_new < 2 ? 2 - n_new : 0u;
-  unsigned long long tot;
-  const unsigned long long ex = warp_excl_scan64(
-      (unsigned long long)need_a | ((unsigned long long)n_fresh << 16) | ((unsigned long long)free_a << 32), &tot);
-  if (lane == 0) {
-    const uint32_t Ka = (uint32_t)(tot & 0xFFFF), Kv = (uint32_t)((tot >> 16) & 0xFFFF);
-    const uint32_t Fa = (uint32_t)((tot >> 32) & 0xFFFF);
-    bool ok = true;
-    unsigned long long rb0, bb0;
-    uint32_t av0;
-    // agents: the warp's stack first; when it runs dry, one global pop
-    // serves this interaction and refills the stack with kRefill slots
-    int ac = W.acount;
-    const uint32_t ta = min((uint32_t)ac, Ka);
-    ac -= (int)ta;
-    const uint32_t ga = Ka - ta, gra = ga ? (uint32_t)kRefill : 0u;
-    ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &rb0, &av0, &bb0) && ok;
-    W.bc[0] = rb0;
-    W.bc[1] = bb0;
-    const uint32_t keep = min((uint32_t)(kAStack - ac) - gra, Fa);
-    W.bc[2] = (unsigned long long)av0 | ((unsigned long long)ta << 20) | ((unsigned long long)ac << 40);
-    W.bc[3] = (unsigned long long)keep | ((Fa > keep ? atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep)) : 0ull) << 16);
-    W.bc[8] = (unsigned long long)ga | ((unsigned long long)gra << 16) | ((unsigned long long)(ac + (int)gra) << 32);
-    W.acount = ac + (int)gra + (int)keep;
-    int vc = W.vcount;
-    const uint32_t tv = min((uint32_t)vc, Kv);
-    vc -= (int)tv;
-    const uint32_t gv = Kv - tv, grv = gv ? (uint32_t)kRefill : 0u;
-    W.vcount = vc + (int)grv;
-    ok = pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &rb0, &av0, &bb0) && ok;
-    W.bc[4] = rb0;
-    W.bc[5] = bb0;
-    W.bc[6] = (unsigned long long)av0 | ((unsigned long long)tv << 20) | ((unsigned long long)vc << 40);
-    W.bc[9] = (unsigned long long)gv | ((unsigned long long)grv << 16);
-    W.bc[7] = ok ? 0ull : 1ull;
-    live += (long long)Ka - (long long)Fa;
-    if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
-    W.vstage_n = 0;
+  // a3: offsets of this lane among the warp's needs (10 bits per field;
+  // a warp needs at most 32 x 8)
+  const uint32_t packed = need_a | (n_fresh << 10) | (free_a << 20);
+  uint32_t inc = packed;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += t;
   }
-  __syncwarp();
-  if (W.bc[7]) valid = false;
-  uint32_t n_link = 0;
+  const uint32_t tot = __shfl_sync(kFull, inc, 31), ex = inc - packed;
+  const uint32_t Ka = tot & 1023u, Kv = (tot >> 10) & 1023u, Fa = tot >> 20;
+  const uint32_t oa = ex & 1023u, ov = (ex >> 10) & 1023u, of = ex >> 20;
+  // the warp's stacks first; when one runs dry, one global pop serves this
+  // interaction and refills the stack with kRefill slots (warp-uniform)
+  const uint32_t ta = min((uint32_t)S.ac, Ka), tv = min((uint32_t)S.vc, Kv);
+  const uint32_t abase = (uint32_t)S.ac - ta, vbase = (uint32_t)S.vc - tv;
+  const uint32_t ga = Ka - ta, gv = Kv - tv;
+  const uint32_t gra = ga ? (uint32_t)kRefill : 0u, grv = gv ? (uint32_t)kRefill : 0u;
+  unsigned long long arb = 0, abb = 0, vrb = 0, vbb = 0;
+  uint32_t aav = 0, vav = 0;
+  if (ga | gv) {
+    uint32_t ok = 1;
+    if (lane == 0) {
+      ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &arb, &aav, &abb) ? 1u : 0u;
+      ok &= pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &vrb, &vav, &vbb) ? 1u : 0u;
+      if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
+    }
+    if (!__shfl_sync(kFull, ok, 0)) return 0u;  // fatal: the loop stops
+    arb = __shfl_sync(kFull, arb, 0);
+    abb = __shfl_sync(kFull, abb, 0);
+    aav = __shfl_sync(kFull, aav, 0);
+    vrb = __shfl_sync(kFull, vrb, 0);
+    vbb = __shfl_sync(kFull, vbb, 0);
+    vav = __shfl_sync(kFull, vav, 0);
+  }
+  if (lane == 0) live += (long long)Ka - (long long)Fa;
   if (valid) {
-    const uint32_t oa = (uint32_t)(ex & 0xFFFF), ov = (uint32_t)((ex >> 16) & 0xFFFF);
-    const unsigned long long b2 = W.bc[2], b6 = W.bc[6];
-    const uint32_t aavail = (uint32_t)(b2 & 0xFFFFF), ta = (uint32_t)((b2 >> 20) & 0xFFFFF), abase = (uint32_t)(b2 >> 40);
-    const uint32_t vavail = (uint32_t)(b6 & 0xFFFFF), tv = (uint32_t)((b6 >> 20) & 0xFFFFF), vbase = (uint32_t)(b6 >> 40);
     W.vals[kValExt + 0][lane] = (uint32_t)ra.y;
     W.vals[kValExt + 1][lane] = (uint32_t)ra.z;
     W.vals[kValExt + 2][lane] = (uint32_t)ra.w;
@@ -209,73 +221,82 @@ __device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int
     W.vals[kValExt + 4][lane] = (uint32_t)rb.z;
     W.vals[kValExt + 5][lane] = (uint32_t)rb.w;
     bool in_range = true;
-#pragma unroll
-    for (int j = 0; j < kMaxNew; j++) {
-      if ((uint32_t)j < n_new) {
-        uint32_t sl;
-        if (j == 0) {
-          sl = a;
-        } else if (j == 1) {
-          sl = b;
-        } else {
-          const uint32_t k = oa + (uint32_t)j - 2;
-          if (k < ta) sl = W.astk[abase + k];
-          else sl = pool_slot(d.afree, d.cap_agents, W.bc[0], aavail, W.bc[1], k - ta);
-          if (sl >= d.cap_agents) in_range = false;
-        }
-        W.vals[kValNew + j][lane] = mk_agent(sl);
-      }
+    if (n_new > 0) W.vals[kValNew + 0][lane] = mk_agent(a);
+    if (n_new > 1) W.vals[kValNew + 1][lane] = mk_agent(b);
+    for (uint32_t j = 2; j < n_new; j++) {
+      const uint32_t k = oa + j - 2;
+      const uint32_t sl = k < ta ? W.astk[abase + k] : pool_slot(d.afree, d.cap_agents, arb, aav, abb, k - ta);
+      if (sl >= d.cap_agents) in_range = false;
+      W.vals[kValNew + j][lane] = mk_agent(sl);
     }
-#pragma unroll
-    for (int v = 0; v < kMaxFresh; v++) {
-      if ((uint32_t)v < n_fresh) {
-        const uint32_t k = ov + (uint32_t)v;
-        uint32_t x;
-        if (k < tv) x = W.vstk[vbase + k];
-        else x = pool_slot(d.vfree, d.cap_vars, W.bc[4], vavail, W.bc[5], k - tv);
-        if (x >= d.cap_vars) in_range = false;
-        else __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's release
-        W.vals[kValFresh + v][lane] = mk_var(x);
-      }
+    for (uint32_t v = 0; v < n_fresh; v++) {
+      const uint32_t k = ov + v;
+      const uint32_t x = k < tv ? W.vstk[vbase + k] : pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, k - tv);
+      if (x >= d.cap_vars) in_range = false;
+      else __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's fence
+      W.vals[kValFresh + v][lane] = mk_var(x);
     }
     if (!in_range) {
       set_error(c, INET_ERR_STATE, 4);
       valid = false;
     }
   }
-  if (valid) {
-    const int32_t head_net = (int32_t)(net << 8);
-#pragma unroll
-    for (int j = 0; j < kMaxNew; j++) {
-      if ((uint32_t)j < n_new) {
-        const uint8_t c0 = T.src[j][0], c1 = T.src[j][1], c2 = T.src[j][2];
-        int4 rec;
-        rec.x = head_net | (int32_t)T.lab[j];
-        rec.y = c0 == kValNone ? 0 : (int32_t)W.vals[c0][lane];
-        rec.z = c1 == kValNone ? 0 : (int32_t)W.vals[c1][lane];
-        rec.w = c2 == kValNone ? 0 : (int32_t)W.vals[c2][lane];
-        st_node(d.node + idx_of(W.vals[kValNew + j][lane]), rec);
+  __syncwarp();  // every taken stack entry has been read
+  // refills of the stacks, then this warp's agent frees on top (or the ring)
+  if (gra | grv) {
+    if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, arb, aav, abb, ga + lane);
+    if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, gv + lane);
+  }
+  const uint32_t atop = abase + gra;
+  const uint32_t keep = min((uint32_t)kAStack - atop, Fa);
+  if (Fa) {
+    unsigned long long over = 0;
+    if (Fa > keep) {
+      if (lane == 0) over = atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep));
+      over = __shfl_sync(kFull, over, 0);
+    }
+    if (free_a) {
+      for (uint32_t f = 0; f < free_a; f++) {
+        const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
+        const uint32_t k = of + f;
+        if (k < keep) W.astk[atop + k] = slot;
+        else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
       }
     }
-    n_link = T.n_link;
+  }
+  S.ac = (int)(atop + keep);
+  S.vc = (int)(vbase + grv);
+  // a2: the new agents' records
+  if (valid) {
+    const uint32_t head_net = net << 8;
+    for (uint32_t j = 0; j < n_new; j++) {
+      const uint32_t w = T.agent[j];
+      int4 rec;
+      rec.x = (int32_t)(head_net | (w & 0xFFu));
+      rec.y = port_val(W, (w >> 8) & 0xFFu, lane);
+      rec.z = port_val(W, (w >> 16) & 0xFFu, lane);
+      rec.w = port_val(W, w >> 24, lane);
+      st_node(d.node + idx_of(W.vals[kValNew + j][lane]), rec);
+    }
   }
   // a4: link.  One fence makes this lane's new records and fresh names
   // visible before an exchange can publish a reference to them; the first
   // exchange of each of the first kBatch equations is then issued back to
   // back, and only second arrivals continue (rarely) with a chase.
-  constexpr int kBatch = 4;
+  constexpr uint32_t kBatch = 4;
   uint32_t np = 0;
-  const uint32_t max_link = __reduce_max_sync(kFull, n_link);
-  if (max_link) {
-    if (valid) __threadfence();
+  const uint32_t nl = valid ? n_link : 0u;
+  if (__any_sync(kFull, nl != 0)) {
+    if (nl) __threadfence();
     uint32_t lt[kBatch], lu[kBatch], lo[kBatch];
 #pragma unroll
-    for (int k = 0; k < kBatch; k++) {
+    for (uint32_t k = 0; k < kBatch; k++) {
       lt[k] = 0;
       lu[k] = 0;
       lo[k] = kEmpty;
-      if ((uint32_t)k < n_link) {
-        uint32_t t = W.vals[T.link[k][0]][lane], u = W.vals[T.link[k][1]][lane];
+      if (k < nl) {
+        const uint32_t lk = T.link[k];
+        uint32_t t = W.vals[lk & 0xFFu][lane], u = W.vals[lk >> 8][lane];
         if (!(is_agent(t) && is_agent(u))) {
           if (!is_var(t)) {
             const uint32_t w = t;
@@ -290,8 +311,8 @@ __device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int
       }
     }
 #pragma unroll
-    for (int k = 0; k < kBatch; k++) {
-      if ((uint32_t)k < n_link) {
+    for (uint32_t k = 0; k < kBatch; k++) {
+      if (k < nl) {
         const uint32_t t = lt[k], u = lu[k];
         if (is_agent(t) && is_agent(u)) {
           W.out[np][lane] = Pair{idx_of(t), idx_of(u)};
@@ -315,75 +336,38 @@ __device__ uint32_t async_interact(const Dev& d, const Template* tmpl, const int
         }
       }
     }
-    for (uint32_t k = kBatch; k < max_link; k++) {
-      if (k < n_link) {
-        Pair out;
-        if (link_async(d, W, W.vals[T.link[k][0]][lane], W.vals[T.link[k][1]][lane], &out)) {
-          W.out[np][lane] = out;
-          np++;
-        }
+    for (uint32_t k = kBatch; k < nl; k++) {
+      const uint32_t lk = T.link[k];
+      Pair out;
+      if (link_async(d, W, W.vals[lk & 0xFFu][lane], W.vals[lk >> 8][lane], &out)) {
+        W.out[np][lane] = out;
+        np++;
       }
     }
   }
   __syncwarp();
-  // refills of the warp's stacks (after every taken entry has been read)
-  if (!W.bc[7]) {
-    const unsigned long long b8 = W.bc[8], b9 = W.bc[9];
-    const uint32_t ga = (uint32_t)(b8 & 0xFFFF), gra = (uint32_t)((b8 >> 16) & 0xFFFF);
-    const uint32_t abase = (uint32_t)(W.bc[2] >> 40), aavail = (uint32_t)(W.bc[2] & 0xFFFFF);
-    if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, W.bc[0], aavail, W.bc[1], ga + lane);
-    const uint32_t gv = (uint32_t)(b9 & 0xFFFF), grv = (uint32_t)((b9 >> 16) & 0xFFFF);
-    const uint32_t vbase = (uint32_t)(W.bc[6] >> 40), vavail = (uint32_t)(W.bc[6] & 0xFFFFF);
-    if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, W.bc[4], vavail, W.bc[5], gv + lane);
-  }
-  // agent frees: on the warp's stack above the refill, or the ring
-  if (valid && free_a) {
-    const uint32_t of = (uint32_t)((ex >> 32) & 0xFFFF);
-    const unsigned long long b3 = W.bc[3];
-    const uint32_t keep = (uint32_t)(b3 & 0xFFFF);
-    const unsigned long long over = b3 >> 16;
-    const uint32_t abase = (uint32_t)(W.bc[8] >> 32);
-    for (uint32_t f = 0; f < free_a; f++) {
-      const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
-      const uint32_t k = of + f;
-      if (k < keep) W.astk[abase + k] = slot;
-      else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
-    }
-  }
-  // freed names: on the warp's stack, the overflow to the ring
-  {
-    const int nv = min(W.vstage_n, kVStageW);
-    const int vc = W.vcount;
-    const int keep = min(kVStack - vc, nv);
+  // names freed while linking: on the warp's stack, the overflow to the ring
+  const int nst = W.vstage_n;
+  if (nst) {
+    const int nv = min(nst, kVStageW);
+    const int keepv = min(kVStack - S.vc, nv);
     unsigned long long over = 0;
-    if (lane == 0 && nv > keep) over = atomicAdd(&c->v_tail, (unsigned long long)(nv - keep));
+    if (lane == 0 && nv > keepv) over = atomicAdd(&c->v_tail, (unsigned long long)(nv - keepv));
     over = __shfl_sync(kFull, over, 0);
     for (int j = lane; j < nv; j += 32) {
-      if (j < keep) W.vstk[vc + j] = W.vstage[j];
-      else __stcg(d.vfree + (over + (unsigned long long)(j - keep)) % d.cap_vars, W.vstage[j]);
+      if (j < keepv) W.vstk[S.vc + j] = W.vstage[j];
+      else __stcg(d.vfree + (over + (unsigned long long)(j - keepv)) % d.cap_vars, W.vstage[j]);
     }
+    S.vc += keepv;
     __syncwarp();
-    if (lane == 0) {
-      W.vcount = vc + keep;
-      W.vstage_n = 0;
-    }
+    if (lane == 0) W.vstage_n = 0;
     __syncwarp();
   }
-  // per-net counters and the rule histogram
-  const unsigned vm = __ballot_sync(kFull, valid);
+  // per-net counters (interactions and the change of pending pairs) and the
+  // rule histogram: one fire-and-forget atomic each
   if (valid) {
-    const unsigned peers = __match_any_sync(vm, net);
-    if (peers == vm) {
-      const uint32_t tp = __reduce_add_sync(vm, np);
-      const uint32_t cnt = __popc(vm);
-      if (lane == __ffs(vm) - 1)
-        atomicAdd(d.netctr + net, (unsigned long long)cnt +
-                                      ((unsigned long long)((long long)tp - (long long)cnt) << kNetPairShift));
-    } else {
-      atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)np - 1) << kNetPairShift));
-    }
-    const unsigned rp = __match_any_sync(vm, (unsigned)T.rule);
-    if (lane == __ffs(rp) - 1) atomicAdd(&hist[T.rule], (uint32_t)__popc(rp));
+    atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)np - 1) << kNetPairShift));
+    atomicAdd(&hist[hdr >> 24], 1u);
   }
   return valid ? np : 0u;
 }
@@ -440,22 +424,17 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t off = 0;
   auto take = [&](size_t n) { off = (off + 15) / 16 * 16; unsigned char* p = smem_raw + off; off += n; return p; };
-  Template* tmpl = reinterpret_cast<Template*>(take(sizeof(Template) * (d.n_tmpl ? d.n_tmpl : 1)));
+  AsyncTpl* tmpl = reinterpret_cast<AsyncTpl*>(take(sizeof(AsyncTpl) * (d.n_tmpl ? d.n_tmpl : 1)));
   WarpMem* wm = reinterpret_cast<WarpMem*>(take(sizeof(WarpMem) * (blockDim.x / 32)));
   uint32_t* hist = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * INET_MAX_RULES));
   int16_t* tab = reinterpret_cast<int16_t*>(take(sizeof(int16_t) * d.n_labels * d.n_labels));
-  const uint32_t nt = d.n_tmpl * (sizeof(Template) / 16);
-  for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x)
-    reinterpret_cast<int4*>(tmpl)[i] = reinterpret_cast<const int4*>(d.tmpl)[i];
+  for (uint32_t i = threadIdx.x; i < d.n_tmpl; i += blockDim.x) tmpl[i] = pack_template(d.tmpl[i]);
   for (uint32_t i = threadIdx.x; i < d.n_labels * d.n_labels; i += blockDim.x) tab[i] = d.table[i];
   for (uint32_t i = threadIdx.x; i < INET_MAX_RULES; i += blockDim.x) hist[i] = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem& W = wm[wid];
-  if (lane == 0) {
-    W.acount = 0;
-    W.vcount = 0;
-    W.vstage_n = 0;
-  }
+  if (lane == 0) W.vstage_n = 0;
+  WarpStacks S{0, 0};
   __syncthreads();
   Ctrl* c = d.ctrl;
   Pair* Q = d.front[d.qcur];
@@ -534,7 +513,7 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
       continue;
     }
     nap = 0;
-    const uint32_t np = async_interact(d, tmpl, tab, hist, W, have, pa, pb, live);
+    const uint32_t np = async_interact(d, tmpl, tab, hist, W, S, have, pa, pb, live);
     // keep the first new pair; queue the rest
     const bool had = have;
     have = np > 0;
@@ -552,19 +531,15 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
     // arena is full.  Under that bound the queue slot a producer needs is
     // held by a claimed ticket whenever it is still occupied: an unclaimed
     // one would put every later ticket, and so more than cap pairs, in flight.
-    long long grow = extra, shrink = had && np == 0 ? -1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      grow += __shfl_xor_sync(kFull, grow, o);
-      shrink += __shfl_xor_sync(kFull, shrink, o);
-    }
+    const long long grow = (long long)__reduce_add_sync(kFull, extra);
+    const long long shrink = -(long long)__reduce_add_sync(kFull, had && np == 0 ? 1u : 0u);
     if (lane == 0 && grow) {
       const long long r =
           (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&c->inflight), (unsigned long long)grow);
       if (r + grow > (long long)cap) set_error(c, INET_ERR_ARENA_FULL, 9);
     }
     __syncwarp();
-    {
+    if (grow) {
       // extra pairs go first to idle lanes of this warp (through shared
       // memory), the rest to the ticket queue
       unsigned inc = extra;
@@ -701,13 +676,13 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
   {
     unsigned long long ab = 0, vb = 0;
     if (lane == 0) {
-      if (W.acount) ab = atomicAdd(&c->a_tail, (unsigned long long)W.acount);
-      if (W.vcount) vb = atomicAdd(&c->v_tail, (unsigned long long)W.vcount);
+      if (S.ac) ab = atomicAdd(&c->a_tail, (unsigned long long)S.ac);
+      if (S.vc) vb = atomicAdd(&c->v_tail, (unsigned long long)S.vc);
     }
     ab = __shfl_sync(kFull, ab, 0);
     vb = __shfl_sync(kFull, vb, 0);
-    for (int j = lane; j < W.acount; j += 32) __stcg(d.afree + (ab + j) % d.cap_agents, W.astk[j]);
-    for (int j = lane; j < W.vcount; j += 32) __stcg(d.vfree + (vb + j) % d.cap_vars, W.vstk[j]);
+    for (int j = lane; j < S.ac; j += 32) __stcg(d.afree + (ab + j) % d.cap_agents, W.astk[j]);
+    for (int j = lane; j < S.vc; j += 32) __stcg(d.vfree + (vb + j) % d.cap_vars, W.vstk[j]);
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < d.n_tmpl; i += blockDim.x)
