@@ -55,6 +55,10 @@ def workload(name: str, rank: int = 0):
         w = W.config3()
         desc = "6 nets Fib(S^n Z), n = 20..25"
         caps = dict(max_agents=1 << 23, max_vars=1 << 23, max_pairs=1 << 20, max_nets=64)
+    elif name == "lsys27":
+        w = W.config5()
+        desc = "one net SymA(r) = S^27 Z: the L-System A -> AB, B -> A after 27 steps (514229 symbols)"
+        caps = dict(max_agents=1 << 22, max_vars=1 << 22, max_pairs=1 << 21, max_nets=16)
     elif name == "chain20k":
         w = W.Workload("chain20k", W.ARITH_RULES, [W.add_net(20000, 0)], [(20000, 0)])
         desc = "one net Add(Z, r) = S^20000 Z: a chain of 20001 dependent interactions"
@@ -65,7 +69,7 @@ def workload(name: str, rank: int = 0):
         caps = dict(max_agents=1 << 25, max_vars=1 << 25, max_pairs=1 << 23, max_nets=128)
     else:
         raise SystemExit(f"unknown workload {name}")
-    return w.nets, desc, caps
+    return w.nets, desc, caps, w.rules
 
 
 # --- algorithmic bytes per interaction ---------------------------------------------
@@ -172,14 +176,14 @@ def oracle_binary() -> str:
     return exe
 
 
-def run_oracle(nets, threads: int):
+def run_oracle(nets, threads: int, rules: str = W.ARITH_RULES):
     """Times the oracle on the host; returns (interactions, seconds)."""
     import tempfile
     exe = oracle_binary()
     with tempfile.TemporaryDirectory() as d:
         rp, np_ = os.path.join(d, "r.txt"), os.path.join(d, "n.txt")
         with open(rp, "w") as f:
-            f.write(W.ARITH_RULES)
+            f.write(rules)
         with open(np_, "w") as f:
             f.write("\n".join(nets) + "\n")
         p = subprocess.run([exe, rp, np_, "--quiet", "--threads", str(threads)], capture_output=True, text=True)
@@ -190,13 +194,13 @@ def run_oracle(nets, threads: int):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    nets, desc, _ = workload(args.workload)
+    nets, desc, _, rules = workload(args.workload)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        run_oracle(nets, cores)
+        run_oracle(nets, cores, rules)
     tot_i, tot_s = 0, 0.0
     for _ in range(args.steps):
-        i, s = run_oracle(nets, cores)
+        i, s = run_oracle(nets, cores, rules)
         tot_i += i
         tot_s += s
     value = tot_i / tot_s
@@ -281,7 +285,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mul2048")
-    ap.add_argument("--mode", default="async", choices=["async", "persistent", "graph", "plain"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "async", "persistent", "graph", "plain"],
+                    help="loop form; auto: the autotuner picks async or persistent for the workload")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--grid", type=int, default=0)
     ap.add_argument("--solo-max", type=int, default=0)
@@ -310,20 +315,22 @@ def main():
         dist.init_process_group("gloo")
     from paper_1404_0076_gb300 import Evaluator
 
-    nets, desc, caps = workload(args.workload, rank)
+    nets, desc, caps, rules_text = workload(args.workload, rank)
     ev = Evaluator(device=local, **caps)
-    ev.load_rules(W.ARITH_RULES)
+    ev.load_rules(rules_text)
     rules = ev.rules()
     bpr = bytes_per_rule(rules, batched=len(nets) > 1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 129 MB L2
     opts = dict(mode=args.mode, block=args.block, grid=args.grid, solo_max=args.solo_max)
     tuned = None
+    if args.mode == "auto" and (args.no_tune or args.block or args.grid or args.solo_max):
+        opts["mode"] = "async"
     if not args.no_tune and not (args.block or args.grid or args.solo_max):
         # launch shape from the autotuner (timed runs outside the measured steps)
         from paper_1404_0076_gb300.autotune import Autotuner
         props = torch.cuda.get_device_properties(local)
         tuned = Autotuner().tune(
-            ev, W.ARITH_RULES, nets, args.mode, gpu=props.name, num_sms=props.multi_processor_count)
+            ev, rules_text, nets, args.mode, gpu=props.name, num_sms=props.multi_processor_count)
         opts.update(tuned)
 
     def prepared():
@@ -360,10 +367,10 @@ def main():
     # k_persistent) or, for the step kernels, per reduction step
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / total_s / 1e9
-    traffic = NCU_TRAFFIC.get((args.workload, args.mode, kernel_source_hash()))
+    traffic = NCU_TRAFFIC.get((args.workload, opts["mode"], kernel_source_hash()))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "bytes_per_interaction": alg_bytes / max(1, ints),
-            "kernel": {"async": "k_async", "persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[args.mode],
+            "kernel": {"async": "k_async", "persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[opts["mode"]],
             "launch_time": "device time of the reduce call (for async: the queue fill, set-up and wind-down "
                            "kernels around k_async add a few microseconds)"}
 
@@ -400,13 +407,18 @@ def main():
         t0 = time.perf_counter()
         ids = ev.load_nets(nets)
         st = ev.reduce(ids, **opts)
-        vals, per_net = ev.readback_nats(ids)   # the numerals, walked on the device
+        if rules_text == W.ARITH_RULES:
+            vals, per_net = ev.readback_nats(ids)   # the numerals, walked on the device
+            assert all(v is not None for v in vals)
+        else:
+            texts = [ev.readback(i) for i in ids]   # the normal forms (->sub / ->col)
+            per_net = [ev.net_info(i)["interactions"] for i in ids]
+            assert all(texts)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         h1, d1 = ev.transfer_bytes()
         e2e_h2d, e2e_d2h = h1 - h0, d1 - d0
         e2e_int = sum(per_net)
-        assert all(v is not None for v in vals)
     e2e = {"value": e2e_int / (statistics.median(e2e_ms) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
            "ms_per_step": statistics.median(e2e_ms)}
@@ -439,7 +451,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        ci, cs = run_oracle(nets, cores)
+        ci, cs = run_oracle(nets, cores, rules_text)
         cpu = {"value": ci / cs, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"whole workload once ({len(nets)} nets, {ci} interactions), {cores} threads"}
 
@@ -452,7 +464,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": desc, "nets_per_rank": len(nets), "interactions_per_step": ints // args.steps,
-                           "mode": args.mode, "block": opts["block"] or 256, "grid": opts["grid"] or "auto",
+                           "mode": opts["mode"], "mode_choice": "autotuned" if args.mode == "auto" and tuned else "given",
+                           "block": opts["block"] or 256, "grid": opts["grid"] or "auto",
                            "launch_shape": "autotuned" if tuned else "given",
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"independent batches, {world} rank(s)"},

@@ -1,6 +1,7 @@
 """Launch-shape autotuner for the reduction loop.
 
-For a batch of nets and a loop form it times a small set of launch shapes
+For a batch of nets and a loop form (or "auto": the two whole-loop forms)
+it times a small set of launch shapes
 on the device and keeps the fastest: threads per block, blocks in the grid
 (grid x block against the frontier sets how many pairs each thread takes per
 step in the step forms; in the asynchronous form every lane holds one pair,
@@ -29,7 +30,13 @@ def default_cache_path() -> str:
 
 
 def candidates(mode: str, num_sms: int) -> list[dict]:
-    """Launch shapes tried for one loop form (grid 0 = the form's default)."""
+    """Launch shapes tried for one loop form (grid 0 = the form's default).
+    "auto" tries the two whole-loop forms and lets the batch decide: the
+    asynchronous loop wins on deep dependency chains, the persistent step
+    loop on very wide frontiers."""
+    if mode == "auto":
+        return ([dict(mode="async", **s) for s in candidates("async", num_sms)] +
+                [dict(mode="persistent", **s) for s in candidates("persistent", num_sms)])
     if mode == "async":
         return [dict(block=b, grid=g) for b in (64, 128, 256)
                 for g in (num_sms // 2, num_sms, 2 * num_sms, 4 * num_sms)]
@@ -103,7 +110,7 @@ class Autotuner:
                     ev.reset()
                     ids = ev.load_nets(nets)
                     ev.stage(ids)
-                    st = ev.reduce([], mode=mode, **shape)
+                    st = ev.reduce([], **({"mode": mode} | shape))
                     best = min(best, st["device_ms"])
                     counts.add(st["interactions"])
             except RuntimeError as e:

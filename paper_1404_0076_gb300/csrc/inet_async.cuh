@@ -283,7 +283,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
   // visible before an exchange can publish a reference to them; the first
   // exchange of each of the first kBatch equations is then issued back to
   // back, and only second arrivals continue (rarely) with a chase.
-  constexpr uint32_t kBatch = 4;
+  constexpr uint32_t kBatch = 2;
   uint32_t np = 0;
   const uint32_t nl = valid ? n_link : 0u;
   if (__any_sync(kFull, nl != 0)) {

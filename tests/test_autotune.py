@@ -67,6 +67,19 @@ def test_shapes_that_disagree_on_the_count_are_an_error(tmp_path):
                                                          num_sms=152)
 
 
+def test_auto_chooses_the_loop_form(tmp_path):
+    class TwoForms(FakeEv):
+        def reduce(self, ids, mode, block=0, grid=0, solo_max=0):
+            r = super().reduce(ids, mode, block, grid, solo_max)
+            if mode == "persistent":
+                r["device_ms"] -= 0.9          # the step loop is faster here
+            return r
+    best = Autotuner(str(tmp_path / "c.json"), reps=1).tune(TwoForms(), "r", ["x"], "auto", num_sms=152)
+    assert best["mode"] == "persistent" and best["block"] == 128
+    shapes = candidates("auto", 152)
+    assert {s["mode"] for s in shapes} == {"async", "persistent"}
+
+
 def test_signature_buckets():
     assert signature(["ab"] * 3) == signature(["abc"] * 3)
     assert signature(["ab"] * 3) != signature(["ab"] * 300)

@@ -458,3 +458,34 @@ def test_nonblocking_readback_overlaps_reduction(orc):
     with pytest.raises(InetError):
         ev.readback_nats_end()
     ev.close()
+
+
+# --- the L-System benchmark (Sec. 5) ---------------------------------------------
+
+@pytest.mark.parametrize("mode", MODES + ["async"])
+def test_lsystem_small(orc, mode):
+    nets = [W.lsys_net(n) for n in (0, 1, 5, 10, 14)]
+    o = orc.run(W.LSYS_RULES, nets, mode="rounds")
+    st, g, tr = run_gpu(W.LSYS_RULES, nets, mode, trace=(mode != "async"))
+    compare(o, g)
+    if mode != "async":
+        assert tr[0] == summed_rounds(o)
+    per_rule = [sum(x["per_rule"][r] for x in o) for r in range(len(o[0]["per_rule"]))]
+    assert st["per_rule"] == per_rule
+
+
+@pytest.mark.parametrize("mode", ["async", "persistent"])
+def test_lsystem_27_full_size(mode):
+    # 514 229 symbols, 2 692 506 interactions: checked against the closed
+    # forms and the word obtained by rewriting the string
+    from tests.test_oracle import leaves, lsys_counts, lsys_word
+    ev = make_ev(max_agents=1 << 22, max_vars=1 << 22, max_pairs=1 << 21)
+    ev.load_rules(W.LSYS_RULES)
+    i = ev.load_net(W.lsys_net(27))
+    st = ev.reduce([i], mode=mode)
+    ints, per_rule = lsys_counts(27)
+    assert st["interactions"] == ints and st["per_rule"] == per_rule
+    info = ev.net_info(i)
+    assert info["interactions"] == ints and info["live_agents"] == 2 * 514229 - 1
+    assert leaves(ev.readback(i)) == lsys_word(27)
+    ev.close()

@@ -251,3 +251,75 @@ def test_errors(oracle):
     bad = oracle.run("Foo(x) = Bar -> x = y;\n", "< | >")[0]
     assert bad.get("rules") == "LINEARITY"
     assert oracle.run(R, W.fib_net(10), max_interactions=100)[0]["status"] == "STEP_LIMIT"
+
+
+# --- the L-System benchmark (Sec. 5: A -> AB, B -> A) -----------------------------
+
+def lsys_word(n: int) -> str:
+    """The L-System word after n steps from A, by plain string rewriting."""
+    w = "A"
+    for _ in range(n):
+        w = "".join("AB" if ch == "A" else "A" for ch in w)
+    return w
+
+
+def fibs(k: int) -> list[int]:
+    f = [0, 1]
+    while len(f) <= k:
+        f.append(f[-1] + f[-2])
+    return f
+
+
+def lsys_counts(n: int) -> tuple[int, list[int]]:
+    """Interactions and per-rule counts of lsys_net(n), derived by hand from
+    the six rules: a symbol with count m > 0 applies its S rule once; SymA
+    also duplicates S^(m-1) Z (m - 1 Dup><S and one Dup><Z) and spawns SymA
+    and SymB with m - 1; SymB becomes SymA with m - 1; at m = 0 a symbol
+    becomes a leaf (one Z rule)."""
+    f = fibs(n + 3)
+    a_expand = f[n + 2] - 1                 # A-symbols over steps 0..n-1: sum fib(i+1)
+    b_expand = f[n + 1] - 1                 # B-symbols over steps 0..n-1: sum fib(i)
+    dup_s = sum(f[i + 1] * (n - i - 1) for i in range(n))
+    per_rule = [f[n + 1], a_expand, f[n], b_expand, a_expand, dup_s]
+    ia, ib = [1], [1]                       # the recursion over the count, as a cross-check
+    for m in range(1, n + 1):
+        ia.append(1 + m + ia[m - 1] + ib[m - 1])
+        ib.append(1 + ia[m - 1])
+    assert ia[n] == sum(per_rule)
+    return ia[n], per_rule
+
+
+def leaves(text: str) -> str:
+    return "".join("A" if t == "LeafA" else "B" for t in text.replace("(", " ").replace(")", " ")
+                   .replace(",", " ").split() if t in ("LeafA", "LeafB"))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 8, 12, 16])
+def test_lsystem_word_counts_and_histogram(oracle, n):
+    r = oracle.run(W.LSYS_RULES, [W.lsys_net(n)])[0]
+    assert r["status"] == "ok"
+    assert leaves(r["result"]) == lsys_word(n)
+    ints, per_rule = lsys_counts(n)
+    assert r["interactions"] == ints and r["per_rule"] == per_rule
+    f = fibs(n + 2)
+    assert r["live"] == 2 * f[n + 2] - 1        # leaves plus the Cat nodes over them
+    assert r["result"].count("Cat(") == f[n + 2] - 1
+
+
+def test_lsystem_grows_in_parallel(oracle):
+    # the rounds schedule: depth linear in n, width exponential (Sec. 5
+    # reports several hundred thousand parallel interactions at n = 27)
+    r = oracle.run(W.LSYS_RULES, [W.lsys_net(20)], mode="rounds", quiet=True)[0]
+    assert sum(r["rounds"]) == lsys_counts(20)[0]
+    assert len(r["rounds"]) <= 3 * 20
+    assert max(r["rounds"]) > 10000
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_lsystem_bruteforce_all_orders(oracle, n):
+    net = W.lsys_net(n)
+    bf = bruteforce.explore(W.LSYS_RULES, net)
+    assert bf["consistent"] and bf["min"] == bf["max"] and len(bf["finals"]) == 1
+    (text, _), = bf["finals"]
+    r = oracle.run(W.LSYS_RULES, [net])[0]
+    assert r["result"] == text and r["interactions"] == bf["min"] == lsys_counts(n)[0]

@@ -58,6 +58,23 @@ Fib2(r) = Z -> r = S(Z);
 Fib2(r) = S(x) -> Dup(a, b) = x, Fib(w1) = S(a), Fib(w2) = b, Add(w2, r) = w1;
 """
 
+# Algae L-System, A -> AB and B -> A (the paper's third benchmark, Sec. 5;
+# the paper prints no rules, so the encoding is ours).  A symbol agent meets
+# the number of iterations still to apply: at zero it becomes a leaf of the
+# result; SymA splits into a concatenation of SymA and SymB, each with its
+# own copy of the remaining count (duplicated by Dup on every step, the
+# drops in parallelism Sec. 5 mentions); SymB becomes SymA.
+LSYS_RULES = """\
+SymA(r) = Z -> r = LeafA;
+SymA(r) = S(k) -> Dup(k1, k2) = k, SymA(x) = k1, SymB(y) = k2, r = Cat(x, y);
+SymB(r) = Z -> r = LeafB;
+SymB(r) = S(k) -> SymA(r) = k;
+Dup(a, b) = Z -> a = Z, b = Z;
+Dup(a, b) = S(x) -> Dup(p, q) = x, a = S(p), b = S(q);
+"""
+
+LSYS_RULE_NAMES = ["SymA><Z", "SymA><S", "SymB><Z", "SymB><S", "Dup><Z", "Dup><S"]
+
 # Rule names in file order (R1..R18), for per-rule histograms.
 ARITH_RULE_NAMES = [
     "Add><Z", "Add><S", "Dup><Z", "Dup><S", "Era><Z", "Era><S",
@@ -266,6 +283,17 @@ def config4(seed: int = SEED_BASE + 4, count: int = 100_000, rate_per_s: float =
             n, s = min(fib_tab, key=lambda kv: abs(math.log(kv[1]) - math.log(t)))
             out.append(Request(float(arrivals[i]), "fib", (n,), s))
     return out
+
+
+def lsys_net(n: int) -> str:
+    """< r | SymA(r) = S^n Z > : r = the L-System word after n steps from A,
+    as a tree of Cat nodes over LeafA / LeafB."""
+    return f"< r | SymA(r) = {numeral(n)} >"
+
+
+def config5(ns=(27,)) -> Workload:
+    """The L-System benchmark: single nets of n = 27 steps (514 229 symbols)."""
+    return Workload("lsys", LSYS_RULES, [lsys_net(n) for n in ns], [(n,) for n in ns], ["lsys"] * len(ns))
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3}
