@@ -72,7 +72,7 @@ def test_auto_chooses_the_loop_form(tmp_path):
         def reduce(self, ids, mode, block=0, grid=0, solo_max=0):
             r = super().reduce(ids, mode, block, grid, solo_max)
             if mode == "persistent":
-                r["device_ms"] -= 0.9          # the step loop is faster here
+                r["device_ms"] = 0.5 + abs(block - 128) / 10   # the step loop is faster here
             return r
     best = Autotuner(str(tmp_path / "c.json"), reps=1).tune(TwoForms(), "r", ["x"], "auto", num_sms=152)
     assert best["mode"] == "persistent" and best["block"] == 128
