@@ -257,6 +257,30 @@ inet_status inet_reset(inet_ctx* ctx);
  * interaction rate beside the HBM roofline. */
 inet_status inet_bench_exch(int device, uint64_t n_slots, uint64_t n_ops, double* exch_per_s_out);
 
+/* ---- Control: the paper's communication phase ------------------------------
+ * Sec. 3.5 resolves ->com by sorting every name-headed equation x = t by the
+ * name and folding adjacent equations x = t, x = s into s = t (reduce_by_key),
+ * one ->com per name and pass, the whole loop repeated until nothing merges
+ * (Sec. 3.6).  inet_control_link runs that method (method 1: stable radix
+ * sort + merge passes, own kernels) or this evaluator's linker (method 0: one
+ * launch of atomic exchanges on name slots, chains chased) on the same
+ * equations, for comparison on one GPU.  Not on the reduction path.
+ *   eq[i]      = t | (uint64_t)u << 32, term words (agent or name); every
+ *                name index < n_vars occurs at most twice (linearity)
+ *   pairs_out  = 2 * cap agent indices: the active pairs found (any order)
+ *   *passes_out = merge passes (method 1) or 1; *ms_out = device time of the
+ *                linking (host reads between passes included for method 1)
+ * Device memory is allocated and freed inside.  INET_ERR_LINEARITY when a
+ * name occurs more than twice or a chain does not end. */
+inet_status inet_control_link(int device, const uint64_t* eq, uint64_t n, uint32_t n_vars, int32_t method,
+                              uint32_t* pairs_out, uint64_t cap, uint64_t* n_pairs_out, uint32_t* passes_out,
+                              double* ms_out);
+
+/* reduce_by_key with equality of adjacent values and + as the fold, the
+ * primitive Sec. 3.5 builds on (its example: 2 0 3 3 3 7 5 5 -> 2 0 9 7 10).
+ * `out` holds at least n values; *n_out gets the number of runs. */
+inet_status inet_control_segsum(int device, const int32_t* in, uint64_t n, int32_t* out, uint64_t* n_out);
+
 /* ---- Reduction without any allocation ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate on their request path: a serving process whose allocator

@@ -42,6 +42,7 @@ EXPORTED = [
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
+    "inet_control_link", "inet_control_segsum",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -109,6 +110,11 @@ def _load():
                                 C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats_begin": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_bench_exch": ([C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_double)], C.c_int32),
+        "inet_control_link": ([C.c_int, C.POINTER(C.c_uint64), C.c_uint64, C.c_uint32, C.c_int32,
+                               C.POINTER(C.c_uint32), C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
+                               C.POINTER(C.c_double)], C.c_int32),
+        "inet_control_segsum": ([C.c_int, C.POINTER(C.c_int32), C.c_uint64, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats_end": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int32,
                                     C.POINTER(C.c_int32)], C.c_int32),
         "inet_trace": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_size_t, C.POINTER(C.c_size_t)],
@@ -264,6 +270,34 @@ def inet_bench_exch(device: int, n_slots: int, n_ops: int) -> float:
     if st != INET_OK:
         raise InetError(st, "inet_bench_exch failed")
     return out.value
+
+
+def inet_control_link(device: int, eq, n_vars: int, method: int):
+    """(pairs as a list of (a, b), passes, ms).  eq: sequence of 64-bit
+    equation words t | u << 32; method 0 = atomic linker, 1 = sort + merge."""
+    n = len(eq)
+    if hasattr(eq, "ctypes"):   # a contiguous numpy uint64 array
+        arr = eq.ctypes.data_as(C.POINTER(C.c_uint64))
+    else:
+        arr = (C.c_uint64 * max(1, n))(*eq)
+    pairs = (C.c_uint32 * max(2, 2 * n))()
+    npairs, passes, ms = C.c_uint64(), C.c_uint32(), C.c_double()
+    st = LIB.inet_control_link(device, arr, n, n_vars, method, pairs, n, C.byref(npairs), C.byref(passes), C.byref(ms))
+    if st != INET_OK:
+        raise InetError(st, "inet_control_link failed")
+    k = npairs.value
+    return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(k)], passes.value, ms.value
+
+
+def inet_control_segsum(device: int, values) -> list[int]:
+    n = len(values)
+    arr = (C.c_int32 * max(1, n))(*values)
+    out = (C.c_int32 * max(1, n))()
+    m = C.c_uint64()
+    st = LIB.inet_control_segsum(device, arr, n, out, C.byref(m))
+    if st != INET_OK:
+        raise InetError(st, "inet_control_segsum failed")
+    return list(out[:m.value])
 
 
 def readback_buffers():

@@ -14,6 +14,7 @@
 #include "inet_async.cuh"
 #include "inet_kernels.cuh"
 #include "inet_micro.cuh"
+#include "inet_control.cuh"
 #include "inet_text.h"
 
 using namespace inet;
@@ -415,6 +416,22 @@ inet_status stage_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
   CK(cudaStreamSynchronize(ctx->stream));
   return INET_OK;
 }
+
+// Device buffers of one control run, freed on every exit.
+struct CtlBufs {
+  std::vector<void*> p;
+  template <class T>
+  bool get(T** out, size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return false;
+    p.push_back(q);
+    *out = static_cast<T*>(q);
+    return true;
+  }
+  ~CtlBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
 
 }  // namespace
 
@@ -1081,6 +1098,121 @@ inet_status inet_bench_exch(int device, uint64_t n_slots, uint64_t n_ops, double
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return st;
+}
+
+inet_status inet_control_link(int device, const uint64_t* eq, uint64_t n, uint32_t n_vars, int32_t method,
+                              uint32_t* pairs_out, uint64_t cap, uint64_t* n_pairs_out, uint32_t* passes_out,
+                              double* ms_out) {
+  if ((n && !eq) || !n_pairs_out || (cap && !pairs_out) || n > 0x7FFFFFFFull || (method != 0 && method != 1))
+    return INET_ERR_INVALID_ARG;
+  int nd = 0;
+  if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) return INET_ERR_NO_DEVICE;
+  DeviceGuard g(device);
+  const uint32_t N = (uint32_t)n;
+  CtlBufs B;
+  unsigned long long* d_eq = nullptr;
+  uint2* d_pairs = nullptr;
+  uint32_t* d_cnt = nullptr;  // n_pairs, n_keep, merged, bad, n_out
+  if (!B.get(&d_eq, N) || !B.get(&d_pairs, N) || !B.get(&d_cnt, 8)) return INET_ERR_CUDA;
+  if (cudaMemcpy(d_eq, eq, sizeof(unsigned long long) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d_cnt, 0, 8 * sizeof(uint32_t)) != cudaSuccess)
+    return INET_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  uint32_t passes = 0, bad = 0;
+  const uint32_t gb = (N + 255) / 256;
+  if (method == 0) {
+    uint32_t* slots = nullptr;
+    if (!B.get(&slots, n_vars) || cudaMemset(slots, 0, sizeof(uint32_t) * std::max<uint32_t>(n_vars, 1)) != cudaSuccess)
+      return INET_ERR_CUDA;
+    cudaEventRecord(e0);
+    if (N) k_ctl_link_atomic<<<gb, 256>>>(d_eq, N, slots, n_vars, d_pairs, d_cnt + 0, d_cnt + 3);
+    cudaEventRecord(e1);
+    passes = 1;
+  } else {
+    uint32_t *k0 = nullptr, *k1 = nullptr, *k2 = nullptr, *counts = nullptr;
+    unsigned long long *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;
+    const uint32_t tiles = std::max<uint32_t>(1, (N + kRsTile - 1) / kRsTile);
+    if (!B.get(&k0, N) || !B.get(&k1, N) || !B.get(&k2, N) || !B.get(&v0, N) || !B.get(&v1, N) || !B.get(&v2, N) ||
+        !B.get(&counts, (size_t)256 * tiles))
+      return INET_ERR_CUDA;
+    int bits = 1;
+    while (bits < 32 && (n_vars >> bits)) bits++;
+    cudaEventRecord(e0);
+    if (N) k_ctl_orient<<<gb, 256>>>(d_eq, N, k0, v0, d_cnt + 1, d_pairs, d_cnt + 0);
+    uint32_t m = 0;
+    cudaMemcpy(&m, d_cnt + 1, 4, cudaMemcpyDeviceToHost);
+    // the loop of Sec. 3.6: sort by name, merge, until no equation merges
+    for (;;) {
+      if (m == 0) break;
+      const uint32_t t = (m + kRsTile - 1) / kRsTile;
+      uint32_t *ks = k0, *kd = k1;
+      unsigned long long *vs = v0, *vd = v1;
+      for (int shift = 0; shift < bits; shift += 8) {
+        k_rs_upsweep<<<t, kRsThreads>>>(ks, m, shift, counts);
+        k_rs_scan<<<1, 1024>>>(counts, 256 * t);
+        k_rs_downsweep<<<t, kRsThreads>>>(ks, vs, m, shift, counts, kd, vd);
+        std::swap(ks, kd);
+        std::swap(vs, vd);
+      }
+      cudaMemset(d_cnt + 2, 0, 4);
+      cudaMemset(d_cnt + 4, 0, 4);
+      k_ctl_merge<<<(m + 255) / 256, 256>>>(ks, vs, m, k2, v2, d_cnt + 4, d_pairs, d_cnt + 0, d_cnt + 2, d_cnt + 3);
+      passes++;
+      uint32_t hc[3] = {0, 0, 0};
+      if (cudaMemcpy(hc, d_cnt + 2, 12, cudaMemcpyDeviceToHost) != cudaSuccess) return INET_ERR_CUDA;
+      m = hc[2];
+      if (hc[0] == 0 || passes > N + 1) break;  // nothing merged: fixpoint
+      std::swap(k0, k2);
+      std::swap(v0, v2);
+    }
+    cudaEventRecord(e1);
+  }
+  if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) return INET_ERR_CUDA;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  uint32_t np = 0;
+  cudaMemcpy(&np, d_cnt + 0, 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(&bad, d_cnt + 3, 4, cudaMemcpyDeviceToHost);
+  if (bad) return INET_ERR_LINEARITY;
+  *n_pairs_out = np;
+  if (pairs_out && np) {
+    std::vector<uint2> hp(np);
+    if (cudaMemcpy(hp.data(), d_pairs, sizeof(uint2) * np, cudaMemcpyDeviceToHost) != cudaSuccess) return INET_ERR_CUDA;
+    for (uint32_t i = 0; i < np && i < cap; i++) {
+      pairs_out[2 * i] = hp[i].x;
+      pairs_out[2 * i + 1] = hp[i].y;
+    }
+  }
+  if (passes_out) *passes_out = passes;
+  if (ms_out) *ms_out = ms;
+  return INET_OK;
+}
+
+inet_status inet_control_segsum(int device, const int32_t* in, uint64_t n, int32_t* out, uint64_t* n_out) {
+  if ((n && (!in || !out)) || !n_out || n > 0x7FFFFFFFull) return INET_ERR_INVALID_ARG;
+  int nd = 0;
+  if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) return INET_ERR_NO_DEVICE;
+  DeviceGuard g(device);
+  *n_out = 0;
+  if (n == 0) return INET_OK;
+  const uint32_t N = (uint32_t)n;
+  CtlBufs B;
+  int32_t *d_in = nullptr, *d_out = nullptr;
+  uint32_t *d_rank = nullptr, *d_n = nullptr;
+  if (!B.get(&d_in, N) || !B.get(&d_out, N) || !B.get(&d_rank, N) || !B.get(&d_n, 1)) return INET_ERR_CUDA;
+  if (cudaMemcpy(d_in, in, sizeof(int32_t) * N, cudaMemcpyHostToDevice) != cudaSuccess) return INET_ERR_CUDA;
+  k_ctl_runs<<<1, 1>>>(d_in, N, d_rank);
+  k_ctl_segsum<<<(N + 255) / 256, 256>>>(d_in, N, d_out, d_n, d_rank);
+  uint32_t m = 0;
+  if (cudaMemcpy(&m, d_n, 4, cudaMemcpyDeviceToHost) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return INET_ERR_CUDA;
+  if (cudaMemcpy(out, d_out, sizeof(int32_t) * m, cudaMemcpyDeviceToHost) != cudaSuccess) return INET_ERR_CUDA;
+  *n_out = m;
+  return INET_OK;
 }
 
 const char* inet_last_error(const inet_ctx* ctx) {

@@ -296,4 +296,51 @@ def config5(ns=(27,)) -> Workload:
     return Workload("lsys", LSYS_RULES, [lsys_net(n) for n in ns], [(n,) for n in ns], ["lsys"] * len(ns))
 
 
+def equation_chains(n_pairs: int, p_more: float = 0.2, n_free: int = 0, n_direct: int = 0,
+                    seed: int = SEED_BASE + 6):
+    """A set of equations as one linking step leaves it, for the linker
+    control: n_pairs pairs of agents, each joined through a chain of
+    1 + Geometric(1 - p_more) - 1 names (A = x1, x1 = x2, .., xk = B),
+    n_direct agent pairs written directly (A = B), and n_free chains from an
+    agent to a name that occurs once (no pair).  Names are numbered at
+    random, every equation is oriented at random and the list is shuffled.
+    Returns (eq, n_vars, expected): eq a uint64 array of t | u << 32 over
+    term words (agent i: 4i + 1, name v: 4v + 2), expected the sorted list
+    of (min, max) agent pairs that linking must produce."""
+    rng = np.random.default_rng(seed)
+    A = lambda i: (i << 2) | 1          # noqa: E731
+    V = lambda v: (v << 2) | 2          # noqa: E731
+    lens = rng.geometric(1.0 - p_more, size=n_pairs)            # >= 1 names per chain
+    flen = rng.geometric(0.5, size=n_free)                      # >= 1 names per free chain
+    n_vars = int(lens.sum() + flen.sum())
+    perm = rng.permutation(n_vars)
+    eqs, expected = [], []
+    nv = agent = 0
+    for k in lens:
+        a, b = agent, agent + 1
+        agent += 2
+        vs = perm[nv:nv + k]
+        nv += int(k)
+        eqs.append((A(a), V(int(vs[0]))))
+        eqs.extend((V(int(vs[j])), V(int(vs[j + 1]))) for j in range(k - 1))
+        eqs.append((V(int(vs[-1])), A(b)))
+        expected.append((a, b))
+    for _ in range(n_direct):
+        eqs.append((A(agent), A(agent + 1)))
+        expected.append((agent, agent + 1))
+        agent += 2
+    for k in flen:
+        vs = perm[nv:nv + k]
+        nv += int(k)
+        eqs.append((A(agent), V(int(vs[0]))))
+        eqs.extend((V(int(vs[j])), V(int(vs[j + 1]))) for j in range(k - 1))
+        agent += 1
+    arr = np.array(eqs, dtype=np.uint64).reshape(-1, 2)
+    flip = rng.random(len(arr)) < 0.5
+    arr[flip] = arr[flip][:, ::-1]
+    arr = arr[rng.permutation(len(arr))]
+    eq = np.ascontiguousarray(arr[:, 0] | (arr[:, 1] << np.uint64(32)))
+    return eq, n_vars, sorted(expected)
+
+
 CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3}
