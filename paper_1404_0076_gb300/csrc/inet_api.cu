@@ -667,7 +667,8 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
     uint32_t q = cur;
     for (;;) {
       d.qcur = q;
-      const uint32_t fill_blocks = (uint32_t)std::min<uint64_t>(65535, (ctx->cfg.max_pairs + 255) / 256);
+      const uint32_t fill_blocks =
+          (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((ctx->cfg.max_pairs + 255) / 256, 8ull * ctx->num_sms));
       k_async_fill<<<fill_blocks, 256, 0, ctx->stream>>>(d);
       k_async_prep<<<1, 1, 0, ctx->stream>>>(d);
       void* args[] = {&d};

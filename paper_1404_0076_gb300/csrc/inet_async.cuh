@@ -691,9 +691,14 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
 
 // Before an asynchronous launch: the current frontier's pairs are tickets
 // 0 .. n0-1, already written; every other cell waits for its first ticket.
+// Only cells an earlier launch used are rewritten (all of them once after a
+// reset), so a short launch does not pay, or flush L2 with, the whole ring.
 __global__ void k_async_fill(Dev d) {
-  const uint32_t n0 = min(d.ctrl->fcount[d.qcur], d.cap_pairs);
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < d.cap_pairs;
+  const Ctrl* c = d.ctrl;
+  const uint32_t n0 = min(c->fcount[d.qcur], d.cap_pairs);
+  const unsigned long long lim =
+      c->qinit ? max(min(c->qdirty, (unsigned long long)d.cap_pairs), (unsigned long long)n0) : d.cap_pairs;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < lim;
        i += (unsigned long long)gridDim.x * blockDim.x)
     d.qseq[i] = i < n0 ? i + 1 : i;
 }
@@ -707,6 +712,7 @@ __global__ void k_async_prep(Dev d) {
   c->a_pub = c->a_tail;
   if (c->v_head > c->v_pub) c->v_head = c->v_pub;
   c->v_pub = c->v_tail;
+  c->qinit = 1;  // the fill before this launch initialised the ring
   c->q_head = 0;
   c->q_tail = n0;
   c->inflight = n0;
@@ -730,6 +736,8 @@ __global__ void k_async_post(Dev d) {
   if (c->v_head > c->v_pub) c->v_head = c->v_pub;
   c->fcount[cur] = 0;
   c->fcount[cur ^ 1u] = n;
+  // cells this launch wrote: tickets below the tail (any after a fatal error)
+  c->qdirty = c->fatal ? (unsigned long long)d.cap_pairs : min(c->q_tail, (unsigned long long)d.cap_pairs);
   c->step = c->step + 1;
   c->done = n == 0 || c->fatal != 0 ? 1u : 0u;
   if (c->live > c->peak_live) c->peak_live = c->live;

@@ -61,6 +61,8 @@ struct Ctrl {
   alignas(128) uint32_t astop;              // 1: stop taking work, drain, exit
   alignas(128) uint32_t quiesce;            // warps that stopped producing
   alignas(128) uint32_t aexit;              // pairs written back to the other frontier buffer
+  uint32_t qinit;                           // queue sequence numbers initialised since the reset
+  unsigned long long qdirty;                // cells [0, qdirty) may hold a previous launch's sequence
 };
 
 // Published step word of the persistent kernel.
