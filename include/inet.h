@@ -207,7 +207,16 @@ inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out
 /* Pending active pairs of each listed net as of the end of the last
  * inet_reduce() (0 = the net is in normal form).  Host-only: no device work,
  * no copy. */
-inet_status inet_net_pending(const inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* pending_out);
+inet_status inet_net_pending(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* pending_out);
+
+/* Nets finished since the last call: every net whose pending pairs are zero
+ * (reduced to normal form, or stopped by INET_ERR_NO_RULE) and that no
+ * earlier call reported, found by one device scan over the counters, so a
+ * request loop learns of completions without copying every net's counter.
+ * At most `cap` (<= 65536) ids go to ids_out, in no particular order; the
+ * rest are reported by the next call.  *n_out gets the number written.  The
+ * paper has no counterpart (Sec. 3.6 ends a whole evaluation). */
+inet_status inet_net_finished(inet_ctx* ctx, int32_t* ids_out, int32_t cap, int32_t* n_out);
 
 /* inet_readback_nat() for many nets at once, walked on the device (one
  * thread per net, following name slots as ->col/->sub do, Theorem 1):

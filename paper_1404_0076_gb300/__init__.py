@@ -117,6 +117,10 @@ class Evaluator:
     def pending(self, net_ids) -> list[int]:
         return capi_lazy.inet_net_pending(self.ctx, list(net_ids))
 
+    def finished(self) -> list[int]:
+        """Nets finished since the last call (device scan of the counters)."""
+        return capi_lazy.inet_net_finished(self.ctx)
+
     def readback_nats(self, net_ids):
         return capi_lazy.inet_readback_nats(self.ctx, list(net_ids))
 

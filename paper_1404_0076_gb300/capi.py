@@ -42,7 +42,7 @@ EXPORTED = [
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
-    "inet_control_link", "inet_control_segsum",
+    "inet_control_link", "inet_control_segsum", "inet_net_finished",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -106,6 +106,7 @@ def _load():
         "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_net_info": ([P, C.c_int32, C.POINTER(inet_net_stats)], C.c_int32),
         "inet_net_pending": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64)], C.c_int32),
+        "inet_net_finished": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)], C.c_int32),
         "inet_readback_nats": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64),
                                 C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats_begin": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
@@ -246,6 +247,14 @@ def inet_net_pending(ctx, net_ids) -> list[int]:
     out = (C.c_uint64 * max(1, len(net_ids)))()
     _check(ctx, LIB.inet_net_pending(ctx, ids, len(net_ids), out))
     return list(out[:len(net_ids)])
+
+
+def inet_net_finished(ctx, cap: int = READ_CHUNK) -> list[int]:
+    """Ids of nets finished since the last call (any order)."""
+    out = (C.c_int32 * max(1, cap))()
+    n = C.c_int32()
+    _check(ctx, LIB.inet_net_finished(ctx, out, cap, C.byref(n)))
+    return list(out[:n.value])
 
 
 def inet_readback_nats(ctx, net_ids) -> tuple[list[int | None], list[int]]:

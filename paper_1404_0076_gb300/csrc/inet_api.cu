@@ -33,8 +33,8 @@ constexpr uint32_t kMaxSolo = 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Layout {
-  size_t ctrl, node, var, front0, front1, qseq, afree, vfree, netctr, netstat, hist, table, tmpl, arity,
-      trace_front, trace_live, rb_root, rb_val, total;
+  size_t ctrl, node, var, front0, front1, qseq, afree, vfree, netctr, netstat, netrep, hist, table, tmpl, arity,
+      trace_front, trace_live, rb_root, rb_val, fin_ids, fin_cnt, total;
 };
 
 inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
@@ -67,6 +67,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.vfree = take(sizeof(uint32_t) * c.max_vars);
   L.netctr = take(sizeof(unsigned long long) * c.max_nets);
   L.netstat = take(sizeof(int32_t) * c.max_nets);
+  L.netrep = take(sizeof(uint32_t) * c.max_nets);
   L.hist = take(sizeof(unsigned long long) * INET_MAX_RULES);
   L.table = take(sizeof(int16_t) * kMaxLabels * kMaxLabels);
   L.tmpl = take(sizeof(Template) * INET_MAX_RULES);
@@ -75,6 +76,8 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.trace_live = take(sizeof(long long) * kTraceCap);
   L.rb_root = take(sizeof(uint32_t) * kReadChunk);
   L.rb_val = take(sizeof(unsigned long long) * kReadChunk);
+  L.fin_ids = take(sizeof(int32_t) * kReadChunk);
+  L.fin_cnt = take(sizeof(uint32_t));
   L.total = take(0) + 256;
   return L;
 }
@@ -121,6 +124,7 @@ struct inet_ctx {
   // device-side per-net copies (after the last reduce)
   std::vector<unsigned long long> h_netctr;
   std::vector<int32_t> h_netstat;
+  bool h_net_valid = true;  // false: the device changed them since the last copy
   // readback snapshot
   bool snap_valid = false;
   std::vector<Node> snap_nodes;
@@ -199,6 +203,7 @@ void fill_dev(inet_ctx* ctx) {
   d.vfree = at<uint32_t>(ctx, L.vfree);
   d.netctr = at<unsigned long long>(ctx, L.netctr);
   d.netstat = at<int32_t>(ctx, L.netstat);
+  d.netrep = at<uint32_t>(ctx, L.netrep);
   d.rule_hist = at<unsigned long long>(ctx, L.hist);
   d.ctrl = at<Ctrl>(ctx, L.ctrl);
   d.table = at<int16_t>(ctx, L.table);
@@ -241,6 +246,7 @@ inet_status clear_device(inet_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.var, 0, sizeof(uint32_t) * ctx->cfg.max_vars, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netctr, 0, sizeof(unsigned long long) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netstat, 0, sizeof(int32_t) * ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.netrep, 0, sizeof(uint32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
   uint32_t never = 0xFFFFFFFFu;
   CK(h2d(ctx, &ctx->dev.ctrl->stop_step, &never, 4));
@@ -294,6 +300,20 @@ inet_status upload_staged(inet_ctx* ctx) {
   ctx->st_v0 = ctx->v_bump;
   ctx->st_net0 = (uint32_t)ctx->nets.size();
   if (any) ctx->snap_valid = false;
+  return INET_OK;
+}
+
+// Host copies of the per-net counters, refreshed from the device when a
+// reduction changed them (nets not uploaded yet keep their host values).
+inet_status ensure_net_counters(inet_ctx* ctx) {
+  if (ctx->h_net_valid || ctx->host_only || !ctx->ws_ready) return INET_OK;
+  const size_t up = std::min<size_t>(ctx->st_net0, ctx->nets.size());
+  if (up) {
+    CK(d2h(ctx, ctx->h_netctr.data(), ctx->dev.netctr, up * sizeof(unsigned long long)));
+    CK(d2h(ctx, ctx->h_netstat.data(), ctx->dev.netstat, up * sizeof(int32_t)));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->h_net_valid = true;
   return INET_OK;
 }
 
@@ -767,12 +787,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   std::vector<unsigned long long> hist(INET_MAX_RULES);
   CK(d2h(ctx, hist.data(), ctx->dev.rule_hist, sizeof(unsigned long long) * INET_MAX_RULES));
   const size_t nn = ctx->nets.size();
-  ctx->h_netctr.resize(nn);
-  ctx->h_netstat.resize(nn);
-  if (nn) {
-    CK(d2h(ctx, ctx->h_netctr.data(), ctx->dev.netctr, nn * sizeof(unsigned long long)));
-    CK(d2h(ctx, ctx->h_netstat.data(), ctx->dev.netstat, nn * sizeof(int32_t)));
-  }
+  ctx->h_net_valid = nn == 0;  // per-net counters are copied when asked for
   CK(cudaStreamSynchronize(ctx->stream));
   float ms = 0;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -850,7 +865,9 @@ inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, 
   if (s) return s;
   if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
   DeviceGuard g(ctx->device);
-  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx))) return s;
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx)) ||
+      (s = ensure_net_counters(ctx)))
+    return s;
   Readback rb;
   read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
            ctx->nets[(size_t)net_id].iface, ctx->rules, (size_t)-1 / 2, true, rb);
@@ -866,7 +883,9 @@ inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out
   if (s) return s;
   if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
   DeviceGuard g(ctx->device);
-  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx))) return s;
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx)) ||
+      (s = ensure_net_counters(ctx)))
+    return s;
   Readback rb;
   read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
            ctx->nets[(size_t)net_id].iface, ctx->rules, 0, false, rb);
@@ -876,8 +895,13 @@ inet_status inet_readback_nat(inet_ctx* ctx, int32_t net_id, uint64_t* value_out
   return INET_OK;
 }
 
-inet_status inet_net_pending(const inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* pending_out) {
+inet_status inet_net_pending(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* pending_out) {
   if (!ctx || n < 0 || (n > 0 && (!net_ids || !pending_out))) return INET_ERR_INVALID_ARG;
+  if (!ctx->host_only) {
+    DeviceGuard g(ctx->device);
+    const inet_status s = ensure_net_counters(ctx);
+    if (s) return s;
+  }
   for (int32_t i = 0; i < n; i++) {
     const int32_t id = net_ids[i];
     if (id < 0 || (size_t)id >= ctx->nets.size() || !ctx->nets[(size_t)id].used) return INET_ERR_INVALID_ARG;
@@ -893,10 +917,13 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
   if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
   if (ctx->rb_n >= 0) return fail(ctx, INET_ERR_STATE, "a non-blocking readback is in flight");
   if (n == 0) return INET_OK;
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  if ((s = upload_staged(ctx)) || (s = ensure_net_counters(ctx))) return s;
   std::vector<uint32_t> roots((size_t)n);
   for (int32_t i = 0; i < n; i++) {
-    inet_status s = check_net(ctx, net_ids[i]);
-    if (s) return s;
+    if ((s = check_net(ctx, net_ids[i]))) return s;
     const NetRec& nr = ctx->nets[(size_t)net_ids[i]];
     roots[(size_t)i] = nr.iface.size() == 1 ? nr.iface[0] : kEmpty;
     if (interactions_out) interactions_out[i] = ctx->h_netctr[(size_t)net_ids[i]] & kNetIntMask;
@@ -907,10 +934,6 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
     for (int32_t i = 0; i < n; i++) values_out[i] = ~0ull;
     return INET_OK;
   }
-  DeviceGuard g(ctx->device);
-  inet_status s = ensure_workspace(ctx);
-  if (s) return s;
-  if ((s = upload_staged(ctx))) return s;
   // roots in, values out, kReadChunk nets at a time
   for (int32_t off = 0; off < n; off += (int32_t)kReadChunk) {
     const int32_t m = std::min<int32_t>(n - off, (int32_t)kReadChunk);
@@ -933,7 +956,7 @@ inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int3
   DeviceGuard g(ctx->device);
   inet_status s = ensure_workspace(ctx);
   if (s) return s;
-  if ((s = upload_staged(ctx))) return s;
+  if ((s = upload_staged(ctx)) || (s = ensure_net_counters(ctx))) return s;
   if (!ctx->rb_stream) {
     CK(cudaStreamCreateWithFlags(&ctx->rb_stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ctx->rb_ready, cudaEventDisableTiming));
@@ -1000,23 +1023,53 @@ inet_status inet_readback_nats_end(inet_ctx* ctx, int32_t wait, uint64_t* values
   return INET_OK;
 }
 
+inet_status inet_net_finished(inet_ctx* ctx, int32_t* ids_out, int32_t cap, int32_t* n_out) {
+  if (!ctx || !n_out || cap < 0 || (cap > 0 && !ids_out)) return INET_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  if ((s = upload_staged(ctx))) return s;
+  const uint32_t nn = (uint32_t)std::min<size_t>(ctx->st_net0, ctx->nets.size());
+  if (nn == 0 || cap == 0) return INET_OK;
+  const uint32_t c = (uint32_t)std::min<int32_t>(cap, (int32_t)kReadChunk);
+  int32_t* dids = at<int32_t>(ctx, ctx->lay.fin_ids);
+  uint32_t* dcnt = at<uint32_t>(ctx, ctx->lay.fin_cnt);
+  static thread_local uint32_t cnt;
+  CK(cudaMemsetAsync(dcnt, 0, 4, ctx->stream));
+  k_net_finished<<<(nn + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, nn, dids, c, dcnt);
+  CK(cudaGetLastError());
+  CK(d2h(ctx, &cnt, dcnt, 4));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const uint32_t k = std::min(cnt, c);
+  if (k) {
+    CK(d2h(ctx, ids_out, dids, sizeof(int32_t) * k));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  *n_out = (int32_t)k;
+  return INET_OK;
+}
+
 inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out) {
   if (!ctx || !out) return INET_ERR_INVALID_ARG;
   inet_status s = check_net(ctx, net_id);
   if (s) return s;
   memset(out, 0, sizeof *out);
   const NetRec& nr = ctx->nets[(size_t)net_id];
-  const unsigned long long v = ctx->h_netctr[(size_t)net_id];
-  out->status = ctx->h_netstat[(size_t)net_id];
-  out->interactions = v & kNetIntMask;
-  out->pending_pairs = v >> kNetPairShift;
-  out->reduced = nr.started && out->pending_pairs == 0 ? 1 : 0;
   if (ctx->host_only) {
     out->pending_pairs = nr.pairs.size();
     return INET_OK;
   }
   DeviceGuard g(ctx->device);
-  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx))) return s;
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx)) ||
+      (s = ensure_net_counters(ctx)))
+    return s;
+  const unsigned long long v = ctx->h_netctr[(size_t)net_id];
+  out->status = ctx->h_netstat[(size_t)net_id];
+  out->interactions = v & kNetIntMask;
+  out->pending_pairs = v >> kNetPairShift;
+  out->reduced = nr.started && out->pending_pairs == 0 ? 1 : 0;
   Readback rb;
   read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(), nr.iface,
            ctx->rules, 0, false, rb);
@@ -1390,6 +1443,7 @@ extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void
   d.vfree = reinterpret_cast<uint32_t*>(fx + kFxVfree);
   d.netctr = reinterpret_cast<unsigned long long*>(fx + kFxNetctr);
   d.netstat = reinterpret_cast<int32_t*>(fx + kFxNetstat);
+  d.netrep = nullptr;  // no inet_net_finished here
   d.rule_hist = reinterpret_cast<unsigned long long*>(fx + kFxHist);
   d.ctrl = reinterpret_cast<Ctrl*>(fx + kFxCtrl);
   d.table = reinterpret_cast<const int16_t*>(fx + kFxTable);

@@ -84,6 +84,7 @@ struct Dev {
   uint32_t* vfree;
   unsigned long long* netctr;
   int32_t* netstat;
+  uint32_t* netrep;      // 1 once inet_net_finished reported the net
   unsigned long long* rule_hist;
   Ctrl* ctrl;
   const int16_t* table;
@@ -1010,6 +1011,20 @@ __global__ void k_read_nats(Dev d, const uint32_t* roots, uint32_t n, int s_labe
     w = (uint32_t)r.y;
   }
   out[i] = res;
+}
+
+// Nets whose pending pairs reached zero and that were not reported before:
+// their ids go to out[0 .. cap) and they are marked reported (nets that do
+// not fit are left for the next call).  Runs between reductions.
+__global__ void k_net_finished(Dev d, uint32_t n_nets, int32_t* out, uint32_t cap, uint32_t* count) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nets || d.netrep[i]) return;
+  if ((__ldcg(d.netctr + i) >> kNetPairShift) != 0) return;
+  const uint32_t k = atomicAdd(count, 1u);
+  if (k < cap) {
+    out[k] = (int32_t)i;
+    d.netrep[i] = 1;
+  }
 }
 
 }  // namespace inet

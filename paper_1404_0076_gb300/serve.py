@@ -4,7 +4,8 @@ Requests (one net each) are admitted as they arrive, while the arena they go
 to has room for them by an estimate of their footprint; every admitted net
 joins the frontier of the nets already in flight (inet_stage), and the
 device runs the asynchronous loop in bounded epochs (slice_us), between
-which finished nets are found (inet_net_pending) and new ones admitted.
+which finished nets are found (inet_net_finished, a device scan that
+reports each net once) and new ones admitted.
 The results of finished nets are read back on a second stream
 (inet_readback_nats_begin / _end) while the device keeps reducing the
 others, so a long readback walk never stalls the loop.  Requests therefore overlap on the device with
@@ -76,6 +77,7 @@ class Server:
         self.nets = [0, 0]          # nets loaded per arena since its reset
         self.inflight = [{}, {}]    # arena -> {net id: (rid, arrival, admitted)}
         self.unstaged = [[], []]    # admitted nets not yet handed to the device
+        self.running = [0, 0]       # admitted nets not finished yet
         self.done_nets = [set(), set()]  # finished, waiting for or in a readback
         self.ready = [[], []]       # finished, readback not yet begun
         self.rb_batch = [None, None]  # nets of the readback in flight
@@ -95,6 +97,7 @@ class Server:
         self.used[k] = 0
         self.nets[k] = 0
         self.unstaged[k] = []
+        self.running[k] = 0
         self.done_nets[k] = set()
         self.ready[k] = []
         self.rb_batch[k] = None
@@ -117,6 +120,7 @@ class Server:
         self.used[k] += need
         self.nets[k] += 1
         self.inflight[k][nid] = (rid, arrival, now)
+        self.running[k] += 1
         return True
 
     # -- device epochs and harvest ------------------------------------------
@@ -128,8 +132,7 @@ class Server:
             if self.unstaged[k]:
                 ev.stage(self.unstaged[k])   # one upload for every net admitted since
                 self.unstaged[k] = []
-            running = [nid for nid in self.inflight[k] if nid not in self.done_nets[k]]
-            if running:
+            if self.running[k]:
                 st = ev.reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
                                check=False)
                 self.epochs += 1
@@ -142,7 +145,8 @@ class Server:
                         done.append(Finished(rid, arr, adm, t, None, 0, st["status"]))
                     self._reset(k)
                     continue
-                fin = [nid for nid, p in zip(running, ev.pending(running)) if p == 0]
+                fin = [nid for nid in ev.finished() if nid in self.inflight[k]]
+                self.running[k] -= len(fin)
                 self.ready[k].extend(fin)
                 self.done_nets[k].update(fin)
             done.extend(self._harvest(k, now_fn, wait=False))

@@ -489,3 +489,36 @@ def test_lsystem_27_full_size(mode):
     assert info["interactions"] == ints and info["live_agents"] == 2 * 514229 - 1
     assert leaves(ev.readback(i)) == lsys_word(27)
     ev.close()
+
+
+def test_finished_nets_are_reported_once(orc):
+    # inet_net_finished reports every net once its pending pairs reach zero:
+    # normal forms, nets with no pair at all, and nets stopped by NO_RULE
+    rules = R + "Foo(x) = Bar -> x = Bar;\n"
+    nets = [W.fib_net(15), W.add_net(5, 2), "< r | r = Z >", "< r | Foo(r) = Z >", W.mul_net(20, 30)]
+    ev = make_ev()
+    ev.load_rules(rules)
+    ids = ev.load_nets(nets)
+    ev.stage(ids)
+    seen = []
+    for _ in range(100000):
+        # a slice that met the missing rule returns NO_RULE, not STEP_LIMIT,
+        # while other nets may still be reducing
+        st = ev.reduce([], mode="async", slice_us=50, check=False)
+        assert st["status"] in ("OK", "STEP_LIMIT", "NO_RULE")
+        seen += ev.finished()
+        if not any(ev.pending(ids)):
+            break
+    seen += ev.finished()
+    assert sorted(seen) == sorted(ids)               # each exactly once
+    assert ev.finished() == []
+    assert ev.pending(ids) == [0] * len(ids)
+    o = orc.run(rules, [nets[0], nets[1], nets[4]])
+    assert [ev.net_info(ids[i])["interactions"] for i in (0, 1, 4)] == [x["interactions"] for x in o]
+    assert ev.net_info(ids[3])["status"] == "NO_RULE"
+    # a net loaded later is reported after it finishes, not before
+    late = ev.load_net(W.add_net(3, 3))
+    assert ev.finished() == []
+    ev.reduce([late], mode="async")
+    assert ev.finished() == [late]
+    ev.close()

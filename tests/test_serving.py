@@ -30,6 +30,7 @@ class FakeEvaluator:
         self.resets = 0
         self.staged = set()
         self.batch = None
+        self.reported = set()
 
     def load_rules(self, text):
         pass
@@ -53,6 +54,11 @@ class FakeEvaluator:
 
     def pending(self, ids):
         return [self.left[i] for i in ids]
+
+    def finished(self):
+        out = [i for i, v in self.left.items() if v == 0 and i not in self.reported]
+        self.reported.update(out)
+        return out
 
     def readback_nats(self, ids):
         return [self.value[i] for i in ids], [self.value[i] // 10 for i in ids]
@@ -79,6 +85,7 @@ class FakeEvaluator:
         self.staged.clear()
         self.next_id = 0
         self.batch = None
+        self.reported.clear()
 
     def close(self):
         pass
