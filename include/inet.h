@@ -174,6 +174,14 @@ inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len);
  * result for the device.  Returns the net id. */
 inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* net_id_out);
 
+/* inet_load_net() for n nets in one call: net i is the text
+ * buf[offsets[i] .. offsets[i+1]) (offsets has n + 1 entries).  The texts
+ * are parsed on several host threads and staged in order; ids_out[i] gets
+ * net i's id.  Stops at the first net that fails (its error is returned) with
+ * *n_loaded_out = the number of nets loaded before it. */
+inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offsets, int32_t n, int32_t* ids_out,
+                           int32_t* n_loaded_out);
+
 /* Adds the active pairs of the listed nets (which must not have been
  * staged or reduced yet; n may be 0) to the frontier and runs the reduction loop of
  * Sec. 3.6 until no active pair remains in the whole context, an error

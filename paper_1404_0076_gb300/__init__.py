@@ -88,7 +88,7 @@ class Evaluator:
         return capi_lazy.inet_load_net(self.ctx, text)
 
     def load_nets(self, texts) -> list[int]:
-        return [capi_lazy.inet_load_net(self.ctx, t) for t in texts]
+        return capi_lazy.inet_load_nets(self.ctx, list(texts))
 
     def reduce(self, net_ids, mode: str = "persistent", block: int = 0, grid: int = 0, solo_max: int = 0,
                max_steps: int = 0, timeout_s: float = 0.0, trace: bool = False, check: bool = True,

@@ -42,7 +42,7 @@ EXPORTED = [
     "inet_stage", "inet_transfer_bytes", "inet_readback", "inet_readback_nat", "inet_net_info",
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
-    "inet_control_link", "inet_control_segsum", "inet_net_finished",
+    "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -107,6 +107,8 @@ def _load():
         "inet_net_info": ([P, C.c_int32, C.POINTER(inet_net_stats)], C.c_int32),
         "inet_net_pending": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64)], C.c_int32),
         "inet_net_finished": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)], C.c_int32),
+        "inet_load_nets": ([P, C.c_char_p, C.POINTER(C.c_uint64), C.c_int32, C.POINTER(C.c_int32),
+                            C.POINTER(C.c_int32)], C.c_int32),
         "inet_readback_nats": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_uint64),
                                 C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats_begin": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
@@ -183,6 +185,22 @@ def inet_rule_info(ctx, rule: int) -> dict:
     _check(ctx, LIB.inet_rule_info(ctx, rule, C.byref(d)))
     return {"name": d.name.decode(), "arity_alpha": d.arity_alpha, "arity_beta": d.arity_beta,
             "n_new": d.n_new, "new_ports": d.new_ports, "n_fresh": d.n_fresh, "n_link": d.n_link}
+
+
+def inet_load_nets(ctx, texts) -> list[int]:
+    """Loads many nets in one call (parsed on several host threads)."""
+    enc = [t.encode() for t in texts]
+    n = len(enc)
+    offs = (C.c_uint64 * (n + 1))()
+    o = 0
+    for i, b in enumerate(enc):
+        offs[i] = o
+        o += len(b)
+    offs[n] = o
+    ids = (C.c_int32 * max(1, n))()
+    done = C.c_int32()
+    _check(ctx, LIB.inet_load_nets(ctx, b"".join(enc), offs, n, ids, C.byref(done)))
+    return list(ids[:n])
 
 
 def inet_load_net(ctx, text: str) -> int:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -616,6 +617,83 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
   ctx->h_netstat.push_back(0);
   ctx->snap_valid = false;
   *net_id_out = (int32_t)slot;
+  return INET_OK;
+}
+
+inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offsets, int32_t n, int32_t* ids_out,
+                           int32_t* n_loaded_out) {
+  if (!ctx || n < 0 || !n_loaded_out || (n > 0 && (!buf || !offsets || !ids_out))) return INET_ERR_INVALID_ARG;
+  *n_loaded_out = 0;
+  if (!ctx->have_rules) return fail(ctx, INET_ERR_STATE, "load rules first");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  for (int32_t i = 0; i < n; i++)
+    if (offsets[i + 1] < offsets[i]) return INET_ERR_INVALID_ARG;
+  if (!ctx->host_only) {
+    DeviceGuard g(ctx->device);
+    inet_status s = ensure_workspace(ctx);
+    if (s) return s;
+  }
+  // parse every net on its own (indices from 0) on a few host threads,
+  // then place them one after another and shift their indices
+  const uint32_t slot0 = (uint32_t)ctx->nets.size();
+  std::vector<FlatNet> fns((size_t)n);
+  std::vector<int> rcs((size_t)n, 0);
+  std::vector<std::string> errs((size_t)n);
+  auto parse = [&](int32_t lo, int32_t hi) {
+    for (int32_t i = lo; i < hi; i++)
+      rcs[(size_t)i] = flatten_net(std::string(buf + offsets[i], offsets[i + 1] - offsets[i]), ctx->rules,
+                                   slot0 + (uint32_t)i, 0, 0, fns[(size_t)i], errs[(size_t)i]);
+  };
+  const int32_t nt = (int32_t)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+  const int32_t T = std::max<int32_t>(1, std::min<int32_t>(nt, n / 64));
+  if (T == 1) {
+    parse(0, n);
+  } else {
+    std::vector<std::thread> th;
+    const int32_t per = (n + T - 1) / T;
+    for (int32_t t = 0; t < T; t++) th.emplace_back(parse, t * per, std::min(n, (t + 1) * per));
+    for (auto& x : th) x.join();
+  }
+  for (int32_t i = 0; i < n; i++) {
+    FlatNet& fn = fns[(size_t)i];
+    if (rcs[(size_t)i]) return fail(ctx, rcs[(size_t)i], errs[(size_t)i]);
+    if (ctx->nets.size() >= ctx->cfg.max_nets) return fail(ctx, INET_ERR_ARENA_FULL, "no free net slot");
+    if (ctx->a_bump + fn.nodes.size() > ctx->cfg.max_agents || ctx->v_bump + fn.vars.size() > ctx->cfg.max_vars)
+      return fail(ctx, INET_ERR_ARENA_FULL, "net does not fit the arena");
+    const uint32_t ab = (uint32_t)ctx->a_bump, vb = (uint32_t)ctx->v_bump;
+    auto shift = [ab, vb](uint32_t w) -> uint32_t {
+      return is_agent(w) ? mk_agent(idx_of(w) + ab) : is_var(w) ? mk_var(idx_of(w) + vb) : w;
+    };
+    for (Node& nd : fn.nodes)
+      for (uint32_t& w : nd.aux) w = shift(w);
+    for (uint32_t& w : fn.vars) w = shift(w);
+    for (uint32_t& w : fn.iface) w = shift(w);
+    for (Pair& p : fn.pairs) {
+      p.a += ab;
+      p.b += ab;
+    }
+    if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
+      ctx->st_a0 = ctx->a_bump;
+      ctx->st_v0 = ctx->v_bump;
+      ctx->st_net0 = (uint32_t)ctx->nets.size();
+    }
+    ctx->st_nodes.insert(ctx->st_nodes.end(), fn.nodes.begin(), fn.nodes.end());
+    ctx->st_vars.insert(ctx->st_vars.end(), fn.vars.begin(), fn.vars.end());
+    ctx->st_netctr.push_back((unsigned long long)fn.pairs.size() << kNetPairShift);
+    ctx->a_bump += fn.nodes.size();
+    ctx->v_bump += fn.vars.size();
+    ctx->live += (int64_t)fn.nodes.size();
+    NetRec nr;
+    nr.used = true;
+    nr.iface = std::move(fn.iface);
+    nr.pairs = std::move(fn.pairs);
+    ctx->nets.push_back(std::move(nr));
+    ctx->h_netctr.push_back((unsigned long long)ctx->nets.back().pairs.size() << kNetPairShift);
+    ctx->h_netstat.push_back(0);
+    ctx->snap_valid = false;
+    ids_out[i] = (int32_t)(ctx->nets.size() - 1);
+    *n_loaded_out = i + 1;
+  }
   return INET_OK;
 }
 

@@ -154,3 +154,32 @@ def test_rules_cannot_change_with_nets_loaded(capi):
     capi.inet_reset(ctx)
     capi.inet_load_rules(ctx, W.ARITH_RULES)
     capi.inet_destroy(ctx)
+
+
+def test_batch_load_matches_one_by_one(capi):
+    nets = W.config1(count=300).nets + [W.fib_net(7)] + \
+        ["< a, b | Dup(a, b) = S(S(Z)) >", "< r | r = Z >"]
+    one, many = host_ctx(capi), host_ctx(capi)
+    for c in (one, many):
+        capi.inet_load_rules(c, W.ARITH_RULES)
+    ids1 = [capi.inet_load_net(one, t) for t in nets]
+    ids2 = capi.inet_load_nets(many, nets)
+    assert ids1 == ids2 == list(range(len(nets)))
+    for i in ids1:
+        assert capi.inet_net_info(one, i)["pending_pairs"] == capi.inet_net_info(many, i)["pending_pairs"]
+    assert capi.inet_load_nets(many, []) == []
+    # staged sizes agree: both contexts need the same workspace for the next net
+    a = capi.inet_load_net(one, W.add_net(3, 3))
+    b = capi.inet_load_nets(many, [W.add_net(3, 3)])[0]
+    assert a == b
+
+
+def test_batch_load_stops_at_the_first_bad_net(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    nets = [W.add_net(1, 1)] * 100 + ["< r | Nope(r) = Z >"] + [W.add_net(2, 2)] * 100
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_load_nets(ctx, nets)
+    assert e.value.name == "PARSE"
+    # the 100 nets before it are loaded; the next id continues after them
+    assert capi.inet_load_net(ctx, W.add_net(0, 0)) == 100
