@@ -522,3 +522,73 @@ def test_finished_nets_are_reported_once(orc):
     ev.reduce([late], mode="async")
     assert ev.finished() == [late]
     ev.close()
+
+
+# --- randomized batches against the oracle (the lock-free queue under stress) -----
+
+def random_batch(rng, n):
+    nets = []
+    for _ in range(n):
+        f = rng.randrange(5)
+        if f == 0:
+            nets.append(W.add_net(rng.randrange(0, 400), rng.randrange(0, 50)))
+        elif f == 1:
+            nets.append(W.mul_net(rng.randrange(0, 25), rng.randrange(0, 25)))
+        elif f == 2:
+            nets.append(W.ack_net(rng.choice([1, 2, 3]), rng.randrange(0, 5)))
+        elif f == 3:
+            nets.append(W.fib_net(rng.randrange(0, 17)))
+        else:
+            nets.append(W.pred_net(rng.randrange(0, 30)))
+    return nets
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_async_random_batches_and_launch_shapes(orc, seed):
+    import random
+    rng = random.Random(14040076 + 100 + seed)
+    nets = random_batch(rng, rng.randrange(1, 400))
+    o = orc.run(R, nets, quiet=True)
+    block = rng.choice([32, 64, 128, 256])
+    grid = rng.choice([1, 2, 7, 0, 152, 600])
+    slice_us = rng.choice([0, 0, 100, 1000])
+    # pairs in flight never exceed half the live agents, plus one per lane
+    # between consuming a pair and counting it out, so this capacity always
+    # suffices while the ticket ring still wraps
+    need = sum(x["peak_live"] for x in o) // 2 + 80000
+    max_pairs = need * rng.choice([1, 2, 4])
+    ev = make_ev(max_pairs=max_pairs)
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    ev.stage(ids)
+    for _ in range(100000):
+        st = ev.reduce([], mode="async", block=block, grid=grid, slice_us=slice_us, check=False)
+        assert st["status"] in ("OK", "STEP_LIMIT"), (st["status"], block, grid, slice_us, max_pairs)
+        if st["status"] == "OK":
+            break
+    vals, ints = ev.readback_nats(ids)
+    assert ints == [x["interactions"] for x in o], (block, grid, slice_us, max_pairs)
+    assert vals == [x["nat"] for x in o], (block, grid, slice_us, max_pairs)
+    for i, x in zip(ids, o):
+        assert ev.net_info(i)["live_agents"] == x["live"]
+    assert sorted(ev.finished()) == sorted(ids)
+    ev.close()
+
+
+def test_async_random_serving_arenas_in_sequence(orc):
+    # several batches through one context with resets in between: queue
+    # cells, stacks and counters start over each time
+    import random
+    rng = random.Random(14040076 + 200)
+    batches = [random_batch(rng, rng.randrange(10, 200)) for _ in range(5)]
+    results = [orc.run(R, nets, quiet=True) for nets in batches]
+    need = max(sum(x["peak_live"] for x in o) for o in results) // 2 + 80000
+    ev = make_ev(max_pairs=need)
+    ev.load_rules(R)
+    for rnd, (nets, o) in enumerate(zip(batches, results)):
+        ids = ev.load_nets(nets)
+        ev.reduce(ids, mode="async", block=rng.choice([64, 256]), grid=rng.choice([0, 304]))
+        vals, ints = ev.readback_nats(ids)
+        assert (vals, ints) == ([x["nat"] for x in o], [x["interactions"] for x in o]), rnd
+        ev.reset()
+    ev.close()
