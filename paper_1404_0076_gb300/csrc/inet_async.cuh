@@ -141,7 +141,8 @@ struct WarpStacks {
 // `live` collects the change of live agents.
 __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl* tmpl, const int16_t* tab,
                                                    uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
-                                                   uint32_t a, uint32_t b, long long& live) {
+                                                   uint32_t a, uint32_t b, long long& live, bool pre,
+                                                   int4 pra, int4 prb) {
   const int lane = threadIdx.x & 31;
   Ctrl* c = d.ctrl;
   uint32_t net = 0, ti = 0;
@@ -151,8 +152,13 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
     valid = false;
   }
   if (valid) {
-    ra = ld_node(d.node + a);
-    rb = ld_node(d.node + b);
+    if (pre) {
+      ra = pra;
+      rb = prb;
+    } else {
+      ra = ld_node(d.node + a);
+      rb = ld_node(d.node + b);
+    }
     const uint32_t la = (uint32_t)ra.x & 0xFFu, lb = (uint32_t)rb.x & 0xFFu;
     const int e = (la < d.n_labels && lb < d.n_labels) ? tab[la * d.n_labels + lb] : -1;
     net = (uint32_t)ra.x >> 8;
@@ -420,7 +426,7 @@ __device__ __forceinline__ bool wait_ticket(const Dev& d, const Pair* Q, unsigne
   }
 }
 
-__global__ void __launch_bounds__(256) k_async(Dev d) {
+__global__ void __launch_bounds__(256, 2) k_async(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t off = 0;
   auto take = [&](size_t n) { off = (off + 15) / 16 * 16; unsigned char* p = smem_raw + off; off += n; return p; };
@@ -446,6 +452,8 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
   long long live = 0;
   uint32_t nap = 0;
   bool stop = false, finished = false;
+  bool pre = false;
+  int4 pra = make_int4(0, 0, 0, 0), prb = pra;
   unsigned long long t_start = 0;
   if (lane == 0) {
     const unsigned long long now = globaltimer();
@@ -513,14 +521,21 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
       continue;
     }
     nap = 0;
-    const uint32_t np = async_interact(d, tmpl, tab, hist, W, S, have, pa, pb, live);
-    // keep the first new pair; queue the rest
+    const uint32_t np = async_interact(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb);
+    // keep the first new pair and start loading its records now, so the
+    // load overlaps the rest of this iteration
     const bool had = have;
     have = np > 0;
+    pre = false;
     if (have) {
       const Pair p0 = W.out[0][lane];
       pa = p0.a;
       pb = p0.b;
+      if (pa < d.cap_agents && pb < d.cap_agents) {
+        pra = ld_node(d.node + pa);
+        prb = ld_node(d.node + pb);
+        pre = true;
+      }
     }
     const uint32_t extra = np > 1 ? np - 1 : 0u;
     // pairs in flight: each new pair beyond a lane's own next one joins
@@ -562,6 +577,11 @@ __global__ void __launch_bounds__(256) k_async(Dev d) {
             pa = p.a;
             pb = p.b;
             have = true;
+            if (pa < d.cap_agents && pb < d.cap_agents) {
+              pra = ld_node(d.node + pa);
+              prb = ld_node(d.node + pb);
+              pre = true;
+            }
           }
         }
         const unsigned toq = totx - local;
