@@ -4,6 +4,19 @@ GPU-based implementation of interaction nets").
 
 `capi` mirrors the C ABI one function per entry point; `Evaluator` wraps a
 context whose device workspace and stream come from PyTorch.
+
+    from paper_1404_0076_gb300 import Evaluator
+    with Evaluator(device=0) as ev:
+        ev.load_rules("Add(y, r) = Z -> r = y;\n"
+                      "Add(y, r) = S(x) -> Add(y, w) = x, r = S(w);\n")
+        ids = ev.load_nets(["< r | Add(S(Z), r) = S(S(Z)) >"])
+        st = ev.reduce(ids, mode="async")      # or "persistent", "graph", "plain"
+        ev.readback(ids[0])                    # 'S(S(S(Z)))'
+        ev.readback_nats(ids)                  # ([3], [3]): value, interactions
+
+Other modules: `serve` (continuous batching of requests over two arenas),
+`autotune` (launch shape and loop form per batch), `shard` (N ranks),
+`build` (compiles the library for sm_103a).
 """
 from __future__ import annotations
 

@@ -592,3 +592,14 @@ def test_async_random_serving_arenas_in_sequence(orc):
         assert (vals, ints) == ([x["nat"] for x in o], [x["interactions"] for x in o]), rnd
         ev.reset()
     ev.close()
+
+
+def test_package_docstring_example():
+    ev = make_ev()
+    with ev:
+        ev.load_rules("Add(y, r) = Z -> r = y;\n"
+                      "Add(y, r) = S(x) -> Add(y, w) = x, r = S(w);\n")
+        ids = ev.load_nets(["< r | Add(S(Z), r) = S(S(Z)) >"])
+        ev.reduce(ids, mode="async")
+        assert ev.readback(ids[0]) == "S(S(S(Z)))"
+        assert ev.readback_nats(ids) == ([3], [3])
