@@ -91,8 +91,8 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "a60a2490fc85"): 11_271_168 + 22_554_880,
-               ("lsys27", "persistent", "a60a2490fc85"): 4_347_648 + 3_587_840}
+NCU_TRAFFIC = {("mul2048", "async", "4175f754c5dc"): 11_664_896 + 24_370_432,
+               ("lsys27", "persistent", "4175f754c5dc"): 4_343_552 + 3_529_728}
 
 
 def kernel_source_hash() -> str:
