@@ -91,16 +91,23 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "4175f754c5dc"): 11_664_896 + 24_370_432,
-               ("lsys27", "persistent", "4175f754c5dc"): 4_343_552 + 3_529_728}
+NCU_TRAFFIC = {("mul2048", "async", "c50feba7a433"): 11_664_896 + 24_370_432,
+               ("lsys27", "persistent", "c50feba7a433"): 4_343_552 + 3_529_728}
 
 
 def kernel_source_hash() -> str:
+    """sha1 prefix of the kernel sources' code (comments and blank lines
+    left out, so a comment edit keeps the key of measured traffic)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for name in ("inet_kernels.cuh", "inet_async.cuh"):
-        with open(os.path.join(ROOT, "paper_1404_0076_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1404_0076_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:12]
 
 

@@ -4,20 +4,25 @@
 // affect another), so nothing forces all pairs of a "loop iteration" to
 // finish before the next begins: every warp of one cooperative launch loops
 // on its own, each lane holding at most one active pair.  An interaction
-// that creates active pairs keeps the first as the lane's next pair, so a
-// sequential chain of interactions never leaves its lane; further pairs go
-// to a FIFO of tickets that idle lanes claim: a bounded ring whose cells
-// carry a 64-bit sequence number each, so that a producer and a consumer
-// of the same cell in different laps can never be confused.  The loop ends when no active
-// pair is left anywhere (the count of pairs in flight reaches zero), as in
-// Sec. 3.6; a time slice or an error instead drains every pair back to a
-// frontier buffer so that the host can resume.
+// that creates active pairs keeps the first as the lane's next pair (and
+// starts loading its records at once), so a sequential chain of
+// interactions never leaves its lane; further pairs go to idle lanes of the
+// same warp, and the rest to a FIFO of tickets that idle lanes claim: a
+// bounded ring whose cells carry a 64-bit sequence number each, so that a
+// producer and a consumer of the same cell in different laps can never be
+// confused.  The loop ends when no active pair is left anywhere (the count
+// of pairs in flight reaches zero), as in Sec. 3.6; a time slice or an error
+// instead drains every pair back to a frontier buffer so that the host can
+// resume.
 //
-// Ordering without barriers: a lane writes its new agent records, then
-// publishes references to them only through release operations (the
-// acq_rel exchange on a name slot, the release store of a cell's sequence);
-// every lane that learns of an agent does so through the matching acquire,
-// so the records it then loads are the ones written.
+// Ordering without barriers: a lane writes its new agent records and fresh
+// names, then one fence, then the exchanges on name slots that publish
+// references to them; the queue publishes a cell with a release store of its
+// sequence and is read with an acquire load; pairs handed to lanes of the
+// same warp pass through shared memory and __syncwarp.  A lane that learns
+// of an agent through an exchange loads its record only after the exchange
+// returned (address dependency), so it sees the record written before the
+// fence.
 #pragma once
 
 #include "inet_kernels.cuh"
