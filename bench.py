@@ -379,6 +379,8 @@ def main():
     traffic = NCU_TRAFFIC.get((args.workload, opts["mode"], kernel_source_hash()))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "bytes_per_interaction": alg_bytes / max(1, ints),
+            # the same fraction at the DRAM bytes ncu measured for one launch
+            "frac_at_traffic": (traffic / (total_s / args.steps) / 1e9) / peak if traffic else None,
             "kernel": {"async": "k_async", "persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[opts["mode"]],
             "launch_time": "device time of the reduce call (for async: the queue fill, set-up and wind-down "
                            "kernels around k_async add a few microseconds)"}
@@ -463,6 +465,11 @@ def main():
         ci, cs = run_oracle(nets, cores, rules_text)
         cpu = {"value": ci / cs, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"whole workload once ({len(nets)} nets, {ci} interactions), {cores} threads"}
+        # and single-threaded, on a bounded sample of the same nets
+        sample = nets[: max(1, min(len(nets), 256))]
+        si, ss = run_oracle(sample, 1, rules_text)
+        cpu["single_thread"] = {"value": si / ss, "unit": UNIT, "cores": 1,
+                                "sample": f"first {len(sample)} nets ({si} interactions), one thread"}
 
     # control: the paper's sort + merge communication phase (Sec. 3.5) on
     # the GPU against the atomic linker, on one synthetic equation set
