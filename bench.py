@@ -439,7 +439,7 @@ def main():
     plain = None
     if not args.no_plain and rank == 0:
         forms = {}
-        for m in ("async", "persistent", "graph"):
+        for m in ("async", "persistent", "graph", "paper"):
             prepared()
             stm = ev.reduce([], mode=m)
             forms[m] = stm["interactions"] / (stm["device_ms"] / 1e3)
@@ -454,7 +454,9 @@ def main():
             torch.cuda.synchronize()
             s1 = ev.reduce([], mode="plain")
             one.append((s1["interactions"], s1["device_ms"]))
-        plain = {"forms": forms, "batch_plain": stp["interactions"] / (stp["device_ms"] / 1e3),
+        plain = {"forms": forms, "forms_note": "paper = the loop of Sec. 3.6 with the sort-based communication of "
+                                               "Sec. 3.5 (own kernels), for comparison",
+                 "batch_plain": stp["interactions"] / (stp["device_ms"] / 1e3),
                  "one_net_per_launch": sum(a for a, _ in one) / (sum(b for _, b in one) / 1e3),
                  "one_net_sample": f"first {len(sample)} nets, each reduced alone by the host-driven loop",
                  "unit": UNIT}

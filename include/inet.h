@@ -75,11 +75,19 @@ enum {
                                conditional WHILE node; no host round trip */
   INET_MODE_PERSISTENT = 2, /* one cooperative launch; a grid barrier between
                                steps; narrow frontiers run on one block */
-  INET_MODE_ASYNC = 3       /* one cooperative launch without steps: every warp
+  INET_MODE_ASYNC = 3,      /* one cooperative launch without steps: every warp
                                reduces pairs as they appear (active pairs are
                                independent, Sec. 2.1); no per-step trace; more
                                than max_pairs pairs in flight at once is
                                INET_ERR_ARENA_FULL */
+  INET_MODE_PAPER = 4       /* the paper's own loop (Sec. 3.6): each step's name
+                               equations are collected, then one communication
+                               pass sorts them by name and folds adjacent pairs
+                               (Sec. 3.5), until neither produced anything; for
+                               comparison.  Runs to the end (max_steps and
+                               slice_us are ignored); needs 2 * max_vars
+                               equations of scratch (36 bytes each, allocated per
+                               call); freed names return to the ring */
 };
 
 typedef struct inet_reduce_opts {

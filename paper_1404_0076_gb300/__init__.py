@@ -25,7 +25,7 @@ import importlib
 # The CUDA library is loaded on first use of `capi` (or anything that needs
 # it), so `paper_1404_0076_gb300.build` can be imported before it exists;
 # using the evaluator without the library raises ImportError.
-MODES = {"plain": 0, "graph": 1, "persistent": 2, "async": 3}
+MODES = {"plain": 0, "graph": 1, "persistent": 2, "async": 3, "paper": 4}
 
 
 def __getattr__(name):

@@ -34,6 +34,7 @@ INET_MODE_PLAIN = 0
 INET_MODE_GRAPH = 1
 INET_MODE_PERSISTENT = 2
 INET_MODE_ASYNC = 3
+INET_MODE_PAPER = 4
 INET_MAX_RULES = 64
 
 EXPORTED = [

@@ -16,6 +16,7 @@
 #include "inet_kernels.cuh"
 #include "inet_micro.cuh"
 #include "inet_control.cuh"
+#include "inet_paper.cuh"
 #include "inet_text.h"
 
 using namespace inet;
@@ -223,6 +224,10 @@ void fill_dev(inet_ctx* ctx) {
   d.slice_ns = kSliceNs;
   d.solo_max = 0;
   d.use_cond = 0;
+  d.paper = 0;
+  d.eq = nullptr;
+  d.eq_n = nullptr;
+  d.cap_eq = 0;
   d.cond = 0;
 }
 
@@ -707,7 +712,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   memset(&o, 0, sizeof o);
   if (opts) o = *opts;
   const int B = o.block ? o.block : 256;
-  if (o.mode < INET_MODE_PLAIN || o.mode > INET_MODE_ASYNC) return fail(ctx, INET_ERR_INVALID_ARG, "bad mode");
+  if (o.mode < INET_MODE_PLAIN || o.mode > INET_MODE_PAPER) return fail(ctx, INET_ERR_INVALID_ARG, "bad mode");
   if (o.mode == INET_MODE_ASYNC) {
     if (B < 32 || B > 256 || B % 32) return fail(ctx, INET_ERR_INVALID_ARG, "ASYNC block must be a multiple of 32 in [32, 256]");
     if (o.max_steps) return fail(ctx, INET_ERR_INVALID_ARG, "ASYNC has no steps; bound a call with slice_us");
@@ -786,6 +791,80 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
         break;
       }
     }
+  } else if (fc[cur] > 0 && o.mode == INET_MODE_PAPER) {
+    // the paper's loop (Sec. 3.6): an interaction phase whose name equations
+    // are collected, then one communication pass (Sec. 3.5: sort by name,
+    // fold adjacent pairs), until neither produced anything
+    const uint64_t cap_eq64 = std::min<uint64_t>(2 * ctx->cfg.max_vars + 1024, 0x7FFFFF00ull);
+    const uint32_t cap_eq = (uint32_t)cap_eq64;
+    const uint32_t tiles_max = (cap_eq + kRsTile - 1) / kRsTile;
+    CtlBufs bufs;
+    unsigned long long *eq = nullptr, *v0 = nullptr, *v1 = nullptr;
+    uint32_t *k0 = nullptr, *k1 = nullptr, *counts = nullptr, *pc = nullptr;
+    if (!bufs.get(&eq, cap_eq) || !bufs.get(&v0, cap_eq) || !bufs.get(&v1, cap_eq) || !bufs.get(&k0, cap_eq) ||
+        !bufs.get(&k1, cap_eq) || !bufs.get(&counts, (size_t)256 * tiles_max) || !bufs.get(&pc, 4))
+      return fail(ctx, INET_ERR_CUDA, "no device memory for the equation arrays of the paper's form");
+    Dev dp = d;
+    dp.paper = 1;
+    dp.eq = eq;
+    dp.eq_n = pc;
+    dp.cap_eq = cap_eq;
+    CK(cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), ctx->stream));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));  // the arrays are set up outside the measured time
+    const uint64_t nv = ctx->v_bump;
+    if (nv) k_paper_collect<<<(unsigned)((nv + 255) / 256), 256, 0, ctx->stream>>>(dp, nv);
+    int bits = 1;
+    while (bits < 32 && (ctx->cfg.max_vars >> bits)) bits++;
+    uint32_t pending = fc[cur];
+    for (;;) {
+      if (pending) {
+        k_paper_prep<<<1, 1, 0, ctx->stream>>>(dp);
+        const uint32_t grid = std::max<uint32_t>(1, (pending + (uint32_t)B - 1) / (uint32_t)B);
+        k_step<<<grid, B, smem, ctx->stream>>>(dp);
+        launches += 2;
+      }
+      CK(cudaMemsetAsync(pc + 1, 0, sizeof(uint32_t), ctx->stream));
+      uint32_t m = 0;
+      CK(d2h(ctx, &m, pc, 4));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (m > cap_eq) return fail(ctx, INET_ERR_ARENA_FULL, "equation array of the paper's form is full");
+      if (m) {
+        const uint32_t t = (m + kRsTile - 1) / kRsTile;
+        k_paper_orient<<<(m + 255) / 256, 256, 0, ctx->stream>>>(dp, m, k0, v0);
+        uint32_t *ks = k0, *kd = k1;
+        unsigned long long *vs = v0, *vd = v1;
+        for (int shift = 0; shift < bits; shift += 8) {
+          k_rs_upsweep<<<t, kRsThreads, 0, ctx->stream>>>(ks, m, shift, counts);
+          k_rs_scan<<<1, 1024, 0, ctx->stream>>>(counts, 256 * t);
+          k_rs_downsweep<<<t, kRsThreads, 0, ctx->stream>>>(ks, vs, m, shift, counts, kd, vd);
+          std::swap(ks, kd);
+          std::swap(vs, vd);
+          launches += 3;
+        }
+        CK(cudaMemsetAsync(pc, 0, sizeof(uint32_t), ctx->stream));  // results compact from 0
+        k_paper_merge<<<(m + 255) / 256, 256, 0, ctx->stream>>>(dp, ks, vs, m, pc + 1);
+        launches += 2;
+      }
+      uint32_t hp[2] = {0, 0}, hs[2] = {0, 0}, fcn[2] = {0, 0};
+      int32_t fat = 0;
+      CK(d2h(ctx, hp, pc, 8));
+      CK(d2h(ctx, hs, &ctx->dev.ctrl->step, 4));
+      CK(d2h(ctx, fcn, ctx->dev.ctrl->fcount, 8));
+      CK(d2h(ctx, &fat, &ctx->dev.ctrl->fatal, 4));
+      CK(cudaStreamSynchronize(ctx->stream));
+      pending = std::min<uint32_t>(fcn[hs[0] & 1u], (uint32_t)ctx->cfg.max_pairs);
+      if (fat) break;
+      if (pending == 0 && hp[1] == 0) break;  // no interaction and no communication: done
+    }
+    // what is left binds its names, as ->com's first arrivals would
+    uint32_t left = 0;
+    CK(d2h(ctx, &left, pc, 4));
+    CK(cudaStreamSynchronize(ctx->stream));
+    left = std::min(left, cap_eq);
+    if (left) k_paper_deposit<<<(left + 255) / 256, 256, 0, ctx->stream>>>(dp, left);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
   } else if (fc[cur] > 0) {
     if (o.mode == INET_MODE_PLAIN) {
       // one launch and one 16-byte read of the frontier size per step

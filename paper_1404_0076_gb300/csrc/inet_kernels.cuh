@@ -85,6 +85,10 @@ struct Dev {
   unsigned long long* netctr;
   int32_t* netstat;
   uint32_t* netrep;      // 1 once inet_net_finished reported the net
+  uint32_t paper;        // the paper's loop form: name equations go to `eq` instead of being linked
+  unsigned long long* eq;  // equations t | u << 32 of the paper's form
+  uint32_t* eq_n;
+  uint32_t cap_eq;
   unsigned long long* rule_hist;
   Ctrl* ctrl;
   const int16_t* table;
@@ -345,6 +349,13 @@ __device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t,
       out->a = idx_of(t);
       out->b = idx_of(u);
       return true;
+    }
+    if (d.paper) {
+      // the paper's form: the equation waits for the communication phase
+      const uint32_t k = atomicAdd(d.eq_n, 1u);
+      if (k < d.cap_eq) d.eq[k] = (unsigned long long)t | ((unsigned long long)u << 32);
+      else set_error(d.ctrl, INET_ERR_ARENA_FULL, 26);
+      return false;
     }
     if (!is_var(t)) {
       uint32_t w = t;

@@ -1,0 +1,121 @@
+// The paper's own loop form (Sec. 3.6, evaluate()): an interaction phase,
+// then one communication phase, repeated until neither an interaction nor a
+// communication happened.  The interaction phase is the step kernel with
+// the name equations of each right-hand side written to an equation array
+// instead of being linked (agent = agent equations are active pairs at
+// once); the communication phase is Sec. 3.5: all name-headed equations are
+// sorted by the name (stable LSD radix sort, inet_control.cuh) and adjacent
+// equations x = t, x = s are folded into s = t, one ->com per name and pass.
+// While this form runs, name bindings live in the equation array only: the
+// bindings already in name slots are collected into it first, and what is
+// left at the end is deposited back, so any loop form can continue.
+#pragma once
+
+#include "inet_control.cuh"
+#include "inet_kernels.cuh"
+
+namespace inet {
+
+// Before a paper-form reduction: every bound name slot becomes an equation
+// x = value and the slot is cleared.
+__global__ void k_paper_collect(Dev d, uint64_t n_vars) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n_vars) return;
+  const uint32_t v = d.var[i];
+  if (v == kEmpty) return;
+  const uint32_t k = atomicAdd(d.eq_n, 1u);
+  if (k < d.cap_eq) {
+    d.eq[k] = (unsigned long long)mk_var((uint32_t)i) | ((unsigned long long)v << 32);
+    d.var[i] = kEmpty;
+  } else {
+    set_error(d.ctrl, INET_ERR_ARENA_FULL, 20);
+  }
+}
+
+// Before an interaction phase: the step kernel runs even when the previous
+// step's frontier came out empty (a communication may have refilled it).
+__global__ void k_paper_prep(Dev d) {
+  Ctrl* c = d.ctrl;
+  c->done = 0;
+  c->hit_slice = 0;
+  c->slice_t0 = 0;
+  __threadfence();
+}
+
+// Communication, step 1: every equation name-first, keyed by the name.
+__global__ void k_paper_orient(Dev d, uint32_t n, uint32_t* keys, unsigned long long* vals) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t t = (uint32_t)d.eq[i], u = (uint32_t)(d.eq[i] >> 32);
+  if (!is_var(t)) {
+    const uint32_t w = t;
+    t = u;
+    u = w;
+  }
+  keys[i] = is_var(t) ? idx_of(t) : 0xFFFFFFFFu;
+  vals[i] = (unsigned long long)t | ((unsigned long long)u << 32);
+}
+
+// Communication, step 2 (after the sort): x = t, x = s become s = t (the
+// functor of Sec. 3.5).  An agent pair joins the frontier of the next
+// interaction phase (and its net's pending count); a name-headed result or
+// an equation without a partner goes back to the equation array.  The name
+// of a merged pair is done and returns to the free ring.
+__global__ void k_paper_merge(Dev d, const uint32_t* keys, const unsigned long long* vals, uint32_t n,
+                              uint32_t* merged) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys[i];
+  if (i > 0 && keys[i - 1] == k) return;  // handled by the first of its group
+  const bool two = i + 1 < n && keys[i + 1] == k && k != 0xFFFFFFFFu;
+  Ctrl* c = d.ctrl;
+  if (two && i + 2 < n && keys[i + 2] == k) set_error(c, INET_ERR_STATE, 21);  // a name seen three times
+  uint32_t t, u;
+  if (two) {
+    t = (uint32_t)(vals[i + 1] >> 32);
+    u = (uint32_t)(vals[i] >> 32);
+    atomicAdd(merged, 1u);
+    const unsigned long long tp = atomicAdd(&c->v_tail, 1ull);
+    __stcg(d.vfree + tp % d.cap_vars, k);
+    if (is_agent(t) && is_agent(u)) {
+      const uint32_t a = idx_of(t), b = idx_of(u);
+      if (a >= d.cap_agents || b >= d.cap_agents) {
+        set_error(c, INET_ERR_STATE, 22);
+        return;
+      }
+      const uint32_t cur = ld_volatile(&c->step) & 1u;
+      const uint32_t p = atomicAdd(&c->fcount[cur], 1u);
+      if (p < d.cap_pairs) {
+        d.front[cur][p] = Pair{a, b};
+        const uint32_t net = (uint32_t)__ldcg(&d.node[a].head) >> 8;
+        if (net < d.max_nets) atomicAdd(d.netctr + net, 1ull << kNetPairShift);
+      } else {
+        set_error(c, INET_ERR_ARENA_FULL, 23);
+      }
+      return;
+    }
+  } else {
+    t = (uint32_t)vals[i];
+    u = (uint32_t)(vals[i] >> 32);
+  }
+  const uint32_t o = atomicAdd(d.eq_n, 1u);
+  if (o < d.cap_eq) d.eq[o] = (unsigned long long)t | ((unsigned long long)u << 32);
+  else set_error(c, INET_ERR_ARENA_FULL, 24);
+}
+
+// After a paper-form reduction: each remaining equation x = t binds its
+// name, as the first arrival of ->com would have left it.
+__global__ void k_paper_deposit(Dev d, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t t = (uint32_t)d.eq[i], u = (uint32_t)(d.eq[i] >> 32);
+  if (!is_var(t)) {
+    const uint32_t w = t;
+    t = u;
+    u = w;
+  }
+  if (is_var(t) && idx_of(t) < d.cap_vars) d.var[idx_of(t)] = u;
+  else set_error(d.ctrl, INET_ERR_STATE, 25);
+}
+
+}  // namespace inet

@@ -603,3 +603,52 @@ def test_package_docstring_example():
         ev.reduce(ids, mode="async")
         assert ev.readback(ids[0]) == "S(S(S(Z)))"
         assert ev.readback_nats(ids) == ([3], [3])
+
+
+# --- the paper's own loop form (Sec. 3.5-3.6) -------------------------------------
+
+@pytest.mark.parametrize("case", golden(), ids=lambda c: c["id"])
+def test_paper_form_examples(orc, case):
+    st, g, _ = run_gpu(case["rules"], [case["net"]], "paper")
+    o = orc.run(case["rules"], [case["net"]])
+    compare(o, g)
+
+
+def test_paper_form_mixed_batch_and_tiles(orc):
+    nets = SMALL + [W.add_net(i % 37, i % 11) for i in range(1002)]
+    o = orc.run(R, nets)
+    st, g, _ = run_gpu(R, nets, "paper", text=True, block=128)
+    compare(o, g)
+    assert st["interactions"] == sum(x["interactions"] for x in o)
+
+
+def test_paper_form_full_add_batch_and_lsystem(orc):
+    nets = W.config0().nets
+    o = orc.run(R, nets, quiet=True)
+    st, g, _ = run_gpu(R, nets, "paper", text=False)
+    compare(o, g, text=False)
+    from tests.test_oracle import leaves, lsys_counts, lsys_word
+    ev = make_ev()
+    ev.load_rules(W.LSYS_RULES)
+    i = ev.load_net(W.lsys_net(16))
+    st = ev.reduce([i], mode="paper")
+    assert (st["interactions"], st["per_rule"]) == lsys_counts(16)
+    assert leaves(ev.readback(i)) == lsys_word(16)
+    ev.close()
+
+
+def test_paper_form_continues_what_another_form_left(orc):
+    # name slots bound by a sliced asynchronous run become equations of the
+    # paper's form, and what the paper's form leaves is read back as usual
+    nets = [W.fib_net(14), W.mul_net(12, 9), W.ack_net(2, 3)]
+    o = orc.run(R, nets)
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    ev.reduce(ids, mode="async", slice_us=30, check=False)
+    ev.reduce([], mode="paper")
+    for k, i in enumerate(ids):
+        assert ev.readback(i) == o[k]["result"]
+        assert ev.net_info(i)["interactions"] == o[k]["interactions"]
+        assert ev.net_info(i)["live_agents"] == o[k]["live"]
+    ev.close()
