@@ -232,3 +232,85 @@ def summarize(done: list[Finished], wall_s: float) -> dict:
             "service_p50_ms": ms(_pct(serv, 50)), "service_p99_ms": ms(_pct(serv, 99)),
             "interactions": ints, "interactions_per_s": ints / wall_s if wall_s > 0 else None,
             "failed": sum(1 for f in done if f.status != "OK")}
+
+
+class MultiServer:
+    """Requests sharded over several devices: one Server per device, each
+    driven by its own host thread, every arrival routed to the device with
+    the least outstanding estimated work.  Requests are independent nets
+    (Sec. 2.1), so no data crosses devices."""
+
+    def __init__(self, rules: str, devices, footprint=default_footprint, make_server=None, **server_kw):
+        import threading
+        if make_server is None:
+            def make_server(dev):
+                return Server(rules, device=dev, footprint=footprint, **server_kw)
+        self.servers = [make_server(dev) for dev in devices]
+        self.footprint = footprint
+        self.lock = threading.Lock()
+        self.load = [0] * len(self.servers)       # estimated work admitted and not finished
+        self.routed = [0] * len(self.servers)
+
+    def close(self):
+        for s in self.servers:
+            s.close()
+
+    def route(self, text: str, size: int) -> int:
+        with self.lock:
+            k = min(range(len(self.servers)), key=lambda i: self.load[i])
+            self.load[k] += size
+            self.routed[k] += 1
+            return k
+
+    def serve(self, requests, time_scale: float = 1.0) -> list[Finished]:
+        """Replays `requests` on the wall clock across the devices."""
+        import threading
+        reqs = sorted(enumerate(requests), key=lambda ir: ir[1].arrival_s)
+        inbox = [collections.deque() for _ in self.servers]
+        done: list[Finished] = []
+        arrived = threading.Event()
+        stop = threading.Event()
+        t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        def worker(k: int):
+            srv = self.servers[k]
+            waiting = collections.deque()
+            while True:
+                while inbox[k]:
+                    waiting.append(inbox[k].popleft())
+                while waiting:
+                    rid, r = waiting[0]
+                    if not srv.try_admit(rid, r.net, r.size, r.arrival_s * time_scale, now()):
+                        break
+                    waiting.popleft()
+                if srv.busy():
+                    fin = srv.epoch(now)
+                    if fin:
+                        with self.lock:
+                            for f in fin:
+                                self.load[k] -= requests[f.rid].size
+                            done.extend(fin)
+                elif stop.is_set() and not waiting and not inbox[k]:
+                    return
+                else:
+                    arrived.wait(0.0005)
+
+        threads = [threading.Thread(target=worker, args=(k,), daemon=True) for k in range(len(self.servers))]
+        for th in threads:
+            th.start()
+        try:
+            for rid, r in reqs:
+                delay = r.arrival_s * time_scale - now()
+                if delay > 0:
+                    time.sleep(delay)
+                inbox[self.route(r.net, r.size)].append((rid, r))
+                arrived.set()
+                arrived.clear()
+        finally:
+            stop.set()
+            for th in threads:
+                th.join()
+        return done

@@ -183,3 +183,42 @@ def test_summary_percentiles_on_cpu():
     assert abs(s["service_p50_ms"] - 451.0) < 1e-9
     assert s["interactions_per_s"] == sum(range(100)) / 2.0
     assert summarize([], 1.0)["p50_ms"] is None
+
+
+def test_requests_shard_over_devices_on_cpu():
+    from paper_1404_0076_gb300.serve import MultiServer
+
+    def make(dev):
+        return Server("", budget_bytes=64 << 20, max_pairs=1 << 10, make_evaluator=FakeEvaluator,
+                      footprint=lambda text, size: 1000)
+    ms = MultiServer("", devices=[0, 1, 2], make_server=make)
+    reqs = [Req(0.0001 * i, f"net:{1 + (i % 7)}", 1 + (i % 7)) for i in range(300)]
+    done = ms.serve(reqs)
+    assert sorted(d.rid for d in done) == list(range(300))
+    for d in done:
+        size = 1 + (d.rid % 7)
+        assert d.value == 10 * size and d.interactions == size
+    # every device got work, and the routing kept their totals close
+    assert all(n > 0 for n in ms.routed) and sum(ms.routed) == 300
+    assert max(ms.routed) - min(ms.routed) <= 100
+    assert ms.load == [0, 0, 0]
+    ms.close()
+
+
+@pytest.mark.gpu
+def test_two_servers_share_the_stream_and_agree_with_the_oracle(oracle):
+    # both on device 0 here (one GPU per box); each has its own contexts and
+    # streams, and their kernels never wait on one another
+    from paper_1404_0076_gb300.serve import MultiServer
+    reqs = mixed_requests(300, seed=14040076 + 5)
+    ms = MultiServer(W.ARITH_RULES, devices=[0, 0], budget_bytes=256 << 20, epoch_us=300, max_pairs=1 << 16)
+    try:
+        done = ms.serve(reqs)
+    finally:
+        ms.close()
+    assert sorted(d.rid for d in done) == list(range(len(reqs)))
+    alone = oracle.run(W.ARITH_RULES, [r.net for r in reqs], quiet=True, threads=8)
+    for d in done:
+        assert d.status == "OK"
+        assert (d.value, d.interactions) == (alone[d.rid]["nat"], alone[d.rid]["interactions"]), d.rid
+    assert all(n > 0 for n in ms.routed)
