@@ -91,8 +91,8 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "c50feba7a433"): 11_664_896 + 24_370_432,
-               ("lsys27", "persistent", "c50feba7a433"): 4_343_552 + 3_529_728}
+NCU_TRAFFIC = {("mul2048", "async", "6ddd982c9ffd"): 11_791_360 + 21_870_080,
+               ("lsys27", "persistent", "6ddd982c9ffd"): 4_345_088 + 3_790_080}
 
 
 def kernel_source_hash() -> str:
