@@ -183,3 +183,36 @@ def test_batch_load_stops_at_the_first_bad_net(capi):
     assert e.value.name == "PARSE"
     # the 100 nets before it are loaded; the next id continues after them
     assert capi.inet_load_net(ctx, W.add_net(0, 0)) == 100
+
+
+def test_argument_errors_are_reported_not_crashed(capi):
+    import ctypes as C
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    L = capi.LIB
+    ids = (C.c_int32 * 4)()
+    n = C.c_int32()
+    # offsets that go backwards, and a null output for a non-empty batch
+    offs = (C.c_uint64 * 3)(0, 10, 5)
+    assert L.inet_load_nets(ctx, b"x" * 10, offs, 2, ids, C.byref(n)) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_load_nets(ctx, b"", offs, 2, None, C.byref(n)) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_load_nets(ctx, None, None, 0, None, C.byref(n)) == capi.INET_OK and n.value == 0
+    # pending and finished on unknown nets / host-only contexts
+    bad = (C.c_int32 * 1)(7)
+    out = (C.c_uint64 * 1)()
+    assert L.inet_net_pending(ctx, bad, 1, out) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_net_finished(ctx, ids, 4, C.byref(n)) == capi.INET_ERR_NO_DEVICE
+    assert L.inet_net_finished(ctx, ids, -1, C.byref(n)) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_readback_nats_begin(ctx, bad, 1) == capi.INET_ERR_NO_DEVICE
+    assert L.inet_readback_nats_begin(ctx, bad, 70000) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_control_link(0, None, 0, 0, 7, None, 0, out, None, None) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_bench_exch(0, 0, 0, None) == capi.INET_ERR_INVALID_ARG
+
+
+def test_reduce_refuses_bad_modes_and_shapes(capi):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    i = capi.inet_load_net(ctx, W.add_net(2, 2))
+    for mode, block in ((9, 256), (capi.INET_MODE_ASYNC, 512), (capi.INET_MODE_PAPER, 16)):
+        st, _ = capi.inet_reduce(ctx, [i], capi.inet_reduce_opts(mode, block, 0, 0, 0, 0, 0, 0), check=False)
+        assert st in (capi.INET_ERR_INVALID_ARG, capi.INET_ERR_NO_DEVICE)
