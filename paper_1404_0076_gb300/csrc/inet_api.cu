@@ -17,6 +17,7 @@
 #include "inet_micro.cuh"
 #include "inet_control.cuh"
 #include "inet_paper.cuh"
+#include "inet_readback.cuh"
 #include "inet_text.h"
 
 using namespace inet;
@@ -25,6 +26,7 @@ namespace {
 
 constexpr uint32_t kTraceCap = 1u << 20;
 constexpr uint32_t kReadChunk = 1u << 16;  // nets per device walk of inet_readback_nats
+constexpr uint32_t kWalkBudget = 128;      // elements one thread walks before the arena is ranked
 constexpr uint64_t kDefaultAgents = 1ull << 22;
 constexpr uint64_t kDefaultVars = 1ull << 22;
 constexpr uint64_t kDefaultPairs = 1ull << 21;
@@ -147,6 +149,11 @@ struct inet_ctx {
   unsigned long long* rb_host_vals = nullptr;
   std::vector<uint64_t> rb_inter;           // interactions of the batch in flight
   int32_t rb_n = -1;                        // nets of the batch in flight, -1: none
+  // list-ranking scratch of the numeral readback: two buffers of
+  // (successor, weight) per agent and name slot, and its control words
+  uint2* jump_buf = nullptr;
+  uint64_t jump_cap = 0;                    // elements per buffer
+  uint32_t* jump_ctl = nullptr;
   std::string err;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -320,6 +327,49 @@ inet_status ensure_net_counters(inet_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
   }
   ctx->h_net_valid = true;
+  return INET_OK;
+}
+
+// Numerals of m nets whose interface words are at droot, into dval, queued
+// on stream st: a walk of kWalkBudget elements per net, then list ranking of
+// the whole arena when some walk ran out (inet_readback.cuh).  The arena is
+// quiescent for these nets (finished), so the slots below the host bump
+// counters hold every element of their lists.  No readback may be in
+// flight when the scratch grows.
+inet_status read_nats_device(inet_ctx* ctx, cudaStream_t st, const uint32_t* droot, uint32_t m, int s_label,
+                             int z_label, unsigned long long* dval) {
+  const uint32_t na = (uint32_t)ctx->a_bump, nv = (uint32_t)ctx->v_bump;
+  const uint64_t n_slots = (uint64_t)na + nv;
+  if (!ctx->jump_ctl) CK(cudaMalloc(&ctx->jump_ctl, sizeof(uint32_t) * kJumpCtl));
+  if (n_slots > ctx->jump_cap) {
+    const uint64_t want = std::min<uint64_t>(std::max<uint64_t>(n_slots, 2 * ctx->jump_cap),
+                                             ctx->cfg.max_agents + ctx->cfg.max_vars);
+    if (ctx->jump_buf) CK(cudaFree(ctx->jump_buf));
+    ctx->jump_buf = nullptr;
+    ctx->jump_cap = 0;
+    CK(cudaMalloc(&ctx->jump_buf, sizeof(uint2) * 2 * want));
+    ctx->jump_cap = want;
+  }
+  uint2* b0 = ctx->jump_buf;
+  uint2* b1 = ctx->jump_buf + ctx->jump_cap;
+  CK(cudaMemsetAsync(ctx->jump_ctl, 0, sizeof(uint32_t) * kJumpCtl, st));
+  const unsigned nb = (m + 255) / 256;
+  k_nat_walk<<<nb, 256, 0, st>>>(ctx->dev, droot, m, na, nv, s_label, z_label, kWalkBudget, dval, ctx->jump_ctl);
+  CK(cudaGetLastError());
+  if (n_slots == 0) return INET_OK;
+  const unsigned grid =
+      (unsigned)std::min<uint64_t>((n_slots + 255) / 256, 8ull * (uint64_t)std::max(ctx->num_sms, 1));
+  k_nat_jump_init<<<grid, 256, 0, st>>>(ctx->dev, na, nv, s_label, z_label, ctx->jump_ctl, b0);
+  CK(cudaGetLastError());
+  // a list of L elements is ranked after ceil(log2 L) rounds, L <= n_slots
+  uint32_t rounds = 1;
+  while ((1ull << rounds) < n_slots) rounds++;
+  for (uint32_t r = 0; r < rounds; r++) {
+    k_nat_jump_round<<<grid, 256, 0, st>>>((uint32_t)n_slots, r, ctx->jump_ctl, b0, b1);
+    k_nat_jump_check<<<nb, 256, 0, st>>>(dval, m, (uint32_t)n_slots, r, ctx->jump_ctl, b0, b1);
+  }
+  k_nat_jump_gather<<<nb, 256, 0, st>>>(dval, m, ctx->jump_ctl, b0, b1);
+  CK(cudaGetLastError());
   return INET_OK;
 }
 
@@ -532,6 +582,8 @@ void inet_destroy(inet_ctx* ctx) {
     if (ctx->rb_after) cudaEventDestroy(ctx->rb_after);
     if (ctx->rb_host_roots) cudaFreeHost(ctx->rb_host_roots);
     if (ctx->rb_host_vals) cudaFreeHost(ctx->rb_host_vals);
+    if (ctx->jump_buf) cudaFree(ctx->jump_buf);
+    if (ctx->jump_ctl) cudaFree(ctx->jump_ctl);
     drop_graph(ctx);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1097,8 +1149,7 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
     uint32_t* droot = at<uint32_t>(ctx, ctx->lay.rb_root);
     unsigned long long* dval = at<unsigned long long>(ctx, ctx->lay.rb_val);
     CK(h2d(ctx, droot, roots.data() + off, sizeof(uint32_t) * (size_t)m));
-    k_read_nats<<<(m + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, droot, (uint32_t)m, si->second, zi->second, dval);
-    CK(cudaGetLastError());
+    if ((s = read_nats_device(ctx, ctx->stream, droot, (uint32_t)m, si->second, zi->second, dval))) return s;
     CK(d2h(ctx, values_out + off, dval, sizeof(unsigned long long) * (size_t)m));
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1142,9 +1193,7 @@ inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int3
     CK(cudaStreamWaitEvent(ctx->rb_stream, ctx->rb_after, 0));
     CK(cudaMemcpyAsync(droot, ctx->rb_host_roots, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
                        ctx->rb_stream));
-    k_read_nats<<<(n + 255) / 256, 256, 0, ctx->rb_stream>>>(ctx->dev, droot, (uint32_t)n, si->second, zi->second,
-                                                             dval);
-    CK(cudaGetLastError());
+    if ((s = read_nats_device(ctx, ctx->rb_stream, droot, (uint32_t)n, si->second, zi->second, dval))) return s;
     CK(cudaMemcpyAsync(ctx->rb_host_vals, dval, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToHost,
                        ctx->rb_stream));
     CK(cudaEventRecord(ctx->rb_ready, ctx->rb_stream));

@@ -460,6 +460,58 @@ def test_nonblocking_readback_overlaps_reduction(orc):
     ev.close()
 
 
+def long_readback_nets():
+    # numerals longer than one thread's walk (list ranking finishes them),
+    # walks that end exactly at the budget, a name chain in front of a
+    # numeral, a long S chain that ends in a non-numeral agent
+    chain = "< r | r = x1, " + ", ".join(f"x{i} = x{i + 1}" for i in range(1, 400)) + f", x400 = {W.numeral(300)} >"
+    nonnat = "< r | r = " + "S(" * 300 + "Add(Z, x)" + ")" * 300 + ", x = Z >"
+    return [W.add_net(3000, 7), W.mul_net(40, 50), W.add_net(0, 129), W.add_net(128, 0), W.add_net(127, 1),
+            W.add_net(63, 1), chain, nonnat, "< a, b | Add(a, b) = Z >", W.add_net(1, 1), W.fib_net(18),
+            W.add_net(0, 0)]
+
+
+@pytest.mark.parametrize("mode", ["async", "persistent"])
+def test_batched_nat_readback_ranks_long_numerals(orc, mode):
+    nets = long_readback_nets()
+    o = orc.run(R, nets)
+    want = [x["nat"] for x in o]
+    assert want[:6] == [3007, 2000, 129, 128, 128, 64] and want[6:8] == [300, None]
+    ev = make_ev()
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    ev.reduce(ids, mode=mode)
+    vals, ints = ev.readback_nats(ids)
+    assert vals == want and ints == [x["interactions"] for x in o]
+    for i, v in zip(ids, vals):
+        if v is not None:
+            assert ev.readback_nat(i)[0] == v
+    # subsets and repeats, blocking and non-blocking
+    sub = [ids[7], ids[0], ids[0], ids[9], ids[1]]
+    assert ev.readback_nats(sub)[0] == [want[7], want[0], want[0], want[9], want[1]]
+    ev.readback_nats_begin(ids[::-1])
+    assert ev.readback_nats_end(wait=True)[0] == want[::-1]
+    # the arena grows: the ranking scratch grows with it
+    more = ev.load_nets([W.mul_net(64, 64), W.add_net(5000, 5000)])
+    ev.reduce(more, mode=mode)
+    assert ev.readback_nats(more + ids[:2])[0] == [4096, 10000, 3007, 2000]
+    ev.close()
+
+
+def test_batched_nat_readback_of_the_full_mul_batch():
+    # all 2048 numerals of the Mul batch (results up to 4096 S agents)
+    w = W.config1()
+    ev = make_ev(max_agents=1 << 24, max_vars=1 << 24, max_pairs=1 << 20, max_nets=4096)
+    ev.load_rules(w.rules)
+    ids = ev.load_nets(w.nets)
+    ev.reduce(ids, mode="async")
+    vals, _ = ev.readback_nats(ids)
+    assert vals == [m * n for m, n in w.params]
+    ev.readback_nats_begin(ids)
+    assert ev.readback_nats_end(wait=True)[0] == vals
+    ev.close()
+
+
 # --- the L-System benchmark (Sec. 5) ---------------------------------------------
 
 @pytest.mark.parametrize("mode", MODES + ["async"])
