@@ -234,20 +234,24 @@ inet_status inet_net_pending(inet_ctx* ctx, const int32_t* net_ids, int32_t n, u
  * paper has no counterpart (Sec. 3.6 ends a whole evaluation). */
 inet_status inet_net_finished(inet_ctx* ctx, int32_t* ids_out, int32_t cap, int32_t* n_out);
 
-/* inet_readback_nat() for many nets at once, walked on the device (one
- * thread per net, following name slots as ->col/->sub do, Theorem 1):
+/* inet_readback_nat() for many nets at once, on the device, following name
+ * slots as ->col/->sub do (Theorem 1): one thread walks each net for at
+ * most 128 elements; numerals that are longer are finished by list ranking
+ * (pointer jumping over every agent and name slot of the arena).
  * values_out[i] = k when net i's interface is one numeral S^k(Z), else
  * UINT64_MAX; interactions_out (may be NULL) gets each net's interaction
- * count.  Copies only 16 bytes per net to the host. */
+ * count.  Copies only 16 bytes per net to the host.  The first call, and
+ * the first after the arena has grown, allocates the ranking scratch
+ * (16 bytes per agent and name slot in use) with cudaMalloc. */
 inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* values_out,
                                uint64_t* interactions_out);
 
 /* inet_readback_nats() without blocking the caller or the main stream: the
- * walk runs on a second stream of the context, after the work queued so far
- * on the main stream and alongside later inet_reduce() calls (finished nets
- * are never touched by the reduction of others, Sec. 2.1).  At most
- * 65536 nets per batch and one batch in flight per context; inet_reset()
- * waits for it and drops its results.  The nets should be finished
+ * walk and the ranking run on a second stream of the context, after the work
+ * queued so far on the main stream and alongside later inet_reduce() calls
+ * (finished nets are never touched by the reduction of others, Sec. 2.1).
+ * At most 65536 nets per batch and one batch in flight per context;
+ * inet_reset() waits for it and drops its results.  The nets should be finished
  * (inet_net_pending() == 0); an unfinished net reads as not-a-numeral or as
  * a partial count.  The paper has no counterpart: it serves a request loop
  * that harvests results while the device keeps reducing. */
