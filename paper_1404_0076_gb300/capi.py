@@ -8,6 +8,7 @@ raises at import time instead of falling back to anything else.
 from __future__ import annotations
 
 import ctypes as C
+import itertools
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -192,12 +193,7 @@ def inet_load_nets(ctx, texts) -> list[int]:
     """Loads many nets in one call (parsed on several host threads)."""
     enc = [t.encode() for t in texts]
     n = len(enc)
-    offs = (C.c_uint64 * (n + 1))()
-    o = 0
-    for i, b in enumerate(enc):
-        offs[i] = o
-        o += len(b)
-    offs[n] = o
+    offs = (C.c_uint64 * (n + 1))(0, *itertools.accumulate(map(len, enc)))
     ids = (C.c_int32 * max(1, n))()
     done = C.c_int32()
     _check(ctx, LIB.inet_load_nets(ctx, b"".join(enc), offs, n, ids, C.byref(done)))

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "host_pool.h"
 #include "inet.h"
 #include "inet_async.cuh"
 #include "inet_kernels.cuh"
@@ -690,67 +691,105 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
     inet_status s = ensure_workspace(ctx);
     if (s) return s;
   }
-  // parse every net on its own (indices from 0) on a few host threads,
-  // then place them one after another and shift their indices
+  // parse every net on its own (indices from 0) on a few host threads;
+  // then, in order, find how many nets load (the first error or the first
+  // net that does not fit ends the batch, the nets before it stay loaded);
+  // then the same threads shift each net's indices to its place and copy it
+  // into the staging vectors
   const uint32_t slot0 = (uint32_t)ctx->nets.size();
   std::vector<FlatNet> fns((size_t)n);
   std::vector<int> rcs((size_t)n, 0);
   std::vector<std::string> errs((size_t)n);
-  auto parse = [&](int32_t lo, int32_t hi) {
+  // body(lo, hi) over [0, cnt) in ranges of 16 nets on the host pool
+  auto on_threads = [](int32_t cnt, const HostPool::Body& body) { HostPool::get().run(cnt, 16, body); };
+  on_threads(n, [&](int32_t lo, int32_t hi) {
     for (int32_t i = lo; i < hi; i++)
       rcs[(size_t)i] = flatten_net(std::string(buf + offsets[i], offsets[i + 1] - offsets[i]), ctx->rules,
                                    slot0 + (uint32_t)i, 0, 0, fns[(size_t)i], errs[(size_t)i]);
-  };
-  const int32_t nt = (int32_t)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
-  const int32_t T = std::max<int32_t>(1, std::min<int32_t>(nt, n / 64));
-  if (T == 1) {
-    parse(0, n);
-  } else {
-    std::vector<std::thread> th;
-    const int32_t per = (n + T - 1) / T;
-    for (int32_t t = 0; t < T; t++) th.emplace_back(parse, t * per, std::min(n, (t + 1) * per));
-    for (auto& x : th) x.join();
-  }
-  for (int32_t i = 0; i < n; i++) {
-    FlatNet& fn = fns[(size_t)i];
-    if (rcs[(size_t)i]) return fail(ctx, rcs[(size_t)i], errs[(size_t)i]);
-    if (ctx->nets.size() >= ctx->cfg.max_nets) return fail(ctx, INET_ERR_ARENA_FULL, "no free net slot");
-    if (ctx->a_bump + fn.nodes.size() > ctx->cfg.max_agents || ctx->v_bump + fn.vars.size() > ctx->cfg.max_vars)
-      return fail(ctx, INET_ERR_ARENA_FULL, "net does not fit the arena");
-    const uint32_t ab = (uint32_t)ctx->a_bump, vb = (uint32_t)ctx->v_bump;
-    auto shift = [ab, vb](uint32_t w) -> uint32_t {
-      return is_agent(w) ? mk_agent(idx_of(w) + ab) : is_var(w) ? mk_var(idx_of(w) + vb) : w;
-    };
-    for (Node& nd : fn.nodes)
-      for (uint32_t& w : nd.aux) w = shift(w);
-    for (uint32_t& w : fn.vars) w = shift(w);
-    for (uint32_t& w : fn.iface) w = shift(w);
-    for (Pair& p : fn.pairs) {
-      p.a += ab;
-      p.b += ab;
+  });
+  std::vector<uint64_t> a_at((size_t)n + 1), v_at((size_t)n + 1);
+  a_at[0] = ctx->a_bump;
+  v_at[0] = ctx->v_bump;
+  int32_t m = 0;
+  inet_status stop = INET_OK;
+  std::string stop_msg;
+  for (; m < n; m++) {
+    const FlatNet& fn = fns[(size_t)m];
+    if (rcs[(size_t)m]) {
+      stop = (inet_status)rcs[(size_t)m];
+      stop_msg = errs[(size_t)m];
+      break;
     }
+    if (ctx->nets.size() + (size_t)m >= ctx->cfg.max_nets) {
+      stop = INET_ERR_ARENA_FULL;
+      stop_msg = "no free net slot";
+      break;
+    }
+    if (a_at[(size_t)m] + fn.nodes.size() > ctx->cfg.max_agents || v_at[(size_t)m] + fn.vars.size() > ctx->cfg.max_vars) {
+      stop = INET_ERR_ARENA_FULL;
+      stop_msg = "net does not fit the arena";
+      break;
+    }
+    a_at[(size_t)m + 1] = a_at[(size_t)m] + fn.nodes.size();
+    v_at[(size_t)m + 1] = v_at[(size_t)m] + fn.vars.size();
+  }
+  if (m > 0) {
     if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
       ctx->st_a0 = ctx->a_bump;
       ctx->st_v0 = ctx->v_bump;
       ctx->st_net0 = (uint32_t)ctx->nets.size();
     }
-    ctx->st_nodes.insert(ctx->st_nodes.end(), fn.nodes.begin(), fn.nodes.end());
-    ctx->st_vars.insert(ctx->st_vars.end(), fn.vars.begin(), fn.vars.end());
-    ctx->st_netctr.push_back((unsigned long long)fn.pairs.size() << kNetPairShift);
-    ctx->a_bump += fn.nodes.size();
-    ctx->v_bump += fn.vars.size();
-    ctx->live += (int64_t)fn.nodes.size();
-    NetRec nr;
-    nr.used = true;
-    nr.iface = std::move(fn.iface);
-    nr.pairs = std::move(fn.pairs);
-    ctx->nets.push_back(std::move(nr));
-    ctx->h_netctr.push_back((unsigned long long)ctx->nets.back().pairs.size() << kNetPairShift);
-    ctx->h_netstat.push_back(0);
+    // staged entries continue the staging vectors: slot a_at[i] is entry
+    // a_at[i] - st_a0 (likewise for names)
+    const size_t na0 = ctx->st_nodes.size(), nv0 = ctx->st_vars.size();
+    ctx->st_nodes.resize(na0 + (size_t)(a_at[(size_t)m] - a_at[0]));
+    ctx->st_vars.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
+    Node* dn = ctx->st_nodes.data() + na0;
+    uint32_t* dv = ctx->st_vars.data() + nv0;
+    on_threads(m, [&](int32_t lo, int32_t hi) {
+      for (int32_t i = lo; i < hi; i++) {
+        FlatNet& fn = fns[(size_t)i];
+        const uint32_t ab = (uint32_t)a_at[(size_t)i], vb = (uint32_t)v_at[(size_t)i];
+        auto shift = [ab, vb](uint32_t w) -> uint32_t {
+          return is_agent(w) ? mk_agent(idx_of(w) + ab) : is_var(w) ? mk_var(idx_of(w) + vb) : w;
+        };
+        Node* o = dn + (a_at[(size_t)i] - a_at[0]);
+        for (const Node& nd : fn.nodes) {
+          Node x = nd;
+          for (uint32_t& w : x.aux) w = shift(w);
+          *o++ = x;
+        }
+        uint32_t* ov = dv + (v_at[(size_t)i] - v_at[0]);
+        for (uint32_t w : fn.vars) *ov++ = shift(w);
+        for (uint32_t& w : fn.iface) w = shift(w);
+        for (Pair& p : fn.pairs) {
+          p.a += ab;
+          p.b += ab;
+        }
+      }
+    });
+    ctx->a_bump = a_at[(size_t)m];
+    ctx->v_bump = v_at[(size_t)m];
+    ctx->live += (int64_t)(a_at[(size_t)m] - a_at[0]);
+    ctx->st_netctr.reserve(ctx->st_netctr.size() + (size_t)m);
+    ctx->nets.reserve(ctx->nets.size() + (size_t)m);
+    for (int32_t i = 0; i < m; i++) {
+      FlatNet& fn = fns[(size_t)i];
+      const unsigned long long ctr = (unsigned long long)fn.pairs.size() << kNetPairShift;
+      ctx->st_netctr.push_back(ctr);
+      NetRec nr;
+      nr.used = true;
+      nr.iface = std::move(fn.iface);
+      nr.pairs = std::move(fn.pairs);
+      ctx->nets.push_back(std::move(nr));
+      ctx->h_netctr.push_back(ctr);
+      ctx->h_netstat.push_back(0);
+      ids_out[i] = (int32_t)(ctx->nets.size() - 1);
+    }
     ctx->snap_valid = false;
-    ids_out[i] = (int32_t)(ctx->nets.size() - 1);
-    *n_loaded_out = i + 1;
+    *n_loaded_out = m;
   }
+  if (stop) return fail(ctx, stop, stop_msg);
   return INET_OK;
 }
 

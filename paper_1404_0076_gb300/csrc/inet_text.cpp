@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cctype>
 #include <cstring>
+#include <string_view>
 #include <unordered_map>
 
 #include "inet.h"
@@ -349,110 +350,209 @@ int compile_rules(const std::string& text, CompiledRules& out, std::string& err)
 // ---------------------------------------------------------------------------
 // Net flattener.
 
-int flatten_net(const std::string& text, const CompiledRules& rules, uint32_t net_slot,
-                uint32_t agent_base, uint32_t var_base, FlatNet& out, std::string& err) {
-  out = FlatNet();
-  std::vector<Tok> toks;
-  if (!tokenize(text, toks, err)) return INET_ERR_PARSE;
-  Reader rd(text, toks);
-  std::vector<Syn> syn;
-  std::vector<int> iface;
-  std::vector<std::pair<int, int>> eqs;
-  if (!rd.need('<', "'<'")) { err = rd.err; return INET_ERR_PARSE; }
-  if (!rd.take('|')) {
-    for (;;) {
-      int t = rd.term(syn);
-      if (t < 0) { err = rd.err; return INET_ERR_PARSE; }
-      iface.push_back(t);
-      if (rd.take('|')) break;
-      if (!rd.need(',', "',' or '|'")) { err = rd.err; return INET_ERR_PARSE; }
-    }
+// Label index of an agent symbol, or -1 (a rule set has at most
+// kMaxLabels symbols, so a scan beats building a string for a map lookup).
+static int label_of(const CompiledRules& rules, std::string_view id) {
+  for (size_t i = 0; i < rules.labels.size(); i++) {
+    const std::string& l = rules.labels[i];
+    if (l.size() == id.size() && memcmp(l.data(), id.data(), id.size()) == 0) return (int)i;
   }
-  if (!rd.take('>')) {
-    for (;;) {
-      int x = rd.term(syn);
-      if (x < 0 || !rd.need('=', "'='")) { err = rd.err; return INET_ERR_PARSE; }
-      int y = rd.term(syn);
-      if (y < 0) { err = rd.err; return INET_ERR_PARSE; }
-      eqs.emplace_back(x, y);
-      if (rd.take('>')) break;
-      if (!rd.need(',', "',' or '>'")) { err = rd.err; return INET_ERR_PARSE; }
-    }
-  }
-  if (rd.p != toks.size()) { err = "text after the end of the net"; return INET_ERR_PARSE; }
-  // names -> slots
-  std::unordered_map<std::string, uint32_t> slot;
+  return -1;
+}
+
+// One pass over the characters: agents are written as their terms are read
+// (pre-order, left to right), names are numbered by first occurrence, and
+// each equation is linked as soon as both sides are read.  The syntax is
+// the tokenizer's: identifiers [A-Za-z][A-Za-z0-9_']*, a name when the
+// first letter is lower-case, '#' comments to the end of the line.
+namespace {
+
+struct NetReader {
+  const std::string& s;
+  const CompiledRules& rules;
+  uint32_t net_slot, agent_base, var_base;
+  FlatNet& out;
+  std::string& err;
+  size_t p = 0;
+  int rc = 0;
+  std::unordered_map<std::string_view, uint32_t> slot;
   std::vector<uint8_t> count;
-  for (size_t n = 0; n < syn.size(); n++) {
-    if (!syn[n].name) continue;
-    std::string id = rd.text(syn[n].tok);
-    auto it = slot.find(id);
-    uint32_t v;
-    if (it == slot.end()) {
-      v = (uint32_t)count.size();
-      slot.emplace(id, v);
-      count.push_back(0);
-    } else v = it->second;
-    if (++count[v] > 2) { err = "name " + id + " occurs more than twice"; return INET_ERR_LINEARITY; }
+  struct Frame {
+    uint32_t node;
+    int port, arity;
+  };
+  std::vector<Frame> frames;
+
+  bool fail(int code, const std::string& msg) {
+    if (!rc) {
+      rc = code;
+      err = msg;
+    }
+    return false;
   }
-  if ((uint64_t)var_base + count.size() > kMaxIndex || (uint64_t)agent_base + syn.size() > kMaxIndex) {
-    err = "net does not fit the index range";
-    return INET_ERR_ARENA_FULL;
+  bool fail_at(const char* what) {
+    return fail(INET_ERR_PARSE, std::string("expected ") + what +
+                                    (p < s.size() ? " at offset " + std::to_string(p) : " at end"));
   }
-  out.vars.assign(count.size(), kEmpty);
-  // agents, built top-down
-  auto build = [&](int root, uint32_t* dst) -> int {
-    struct Item { int n; uint32_t* dst; int64_t parent; int port; };
-    std::vector<Item> st{{root, dst, -1, 0}};
-    while (!st.empty()) {
-      Item it = st.back();
-      st.pop_back();
-      const Syn& s = syn[(size_t)it.n];
-      uint32_t w;
-      if (s.name) {
-        w = mk_var(var_base + slot[rd.text(s.tok)]);
+  void skip() {
+    while (p < s.size()) {
+      const char c = s[p];
+      if (c == '#') {
+        while (p < s.size() && s[p] != '\n') p++;
+      } else if (isspace((unsigned char)c)) {
+        p++;
       } else {
-        std::string id = rd.text(s.tok);
-        auto li = rules.index.find(id);
-        if (li == rules.index.end()) { err = "unknown agent symbol " + id; return INET_ERR_PARSE; }
-        if (rules.arity[(size_t)li->second] != s.nkids) { err = "wrong arity for " + id; return INET_ERR_PARSE; }
-        uint32_t me = (uint32_t)out.nodes.size();
+        break;
+      }
+    }
+  }
+  // the next character after blanks, or 0 at the end
+  char peek() {
+    skip();
+    return p < s.size() ? s[p] : '\0';
+  }
+  bool take(char c) {
+    if (peek() != c) return false;
+    p++;
+    return true;
+  }
+  bool ident(std::string_view& id) {
+    if (!isalpha((unsigned char)peek())) return false;
+    const size_t b = p++;
+    while (p < s.size() && (isalnum((unsigned char)s[p]) || s[p] == '_' || s[p] == '\'')) p++;
+    id = std::string_view(s).substr(b, p - b);
+    return true;
+  }
+  bool bad_char() {
+    const char c = peek();
+    if (c && !isalpha((unsigned char)c) && !strchr("(),=|<>;", c) && !(c == '-' && p + 1 < s.size() && s[p + 1] == '>'))
+      return fail(INET_ERR_PARSE, "unexpected character '" + std::string(1, c) + "' at offset " + std::to_string(p));
+    return true;
+  }
+
+  // One term; *w gets its word.
+  bool term(uint32_t* w_out) {
+    frames.clear();
+    for (;;) {
+      std::string_view id;
+      if (!bad_char()) return false;
+      if (!ident(id)) return fail_at("a term");
+      uint32_t w;
+      bool opened = false;
+      uint32_t me = 0;
+      int arity = 0;
+      if (islower((unsigned char)id[0])) {
+        auto it = slot.find(id);
+        uint32_t v;
+        if (it == slot.end()) {
+          v = (uint32_t)count.size();
+          slot.emplace(id, v);
+          count.push_back(0);
+          out.vars.push_back(kEmpty);
+        } else {
+          v = it->second;
+        }
+        if (++count[v] > 2) return fail(INET_ERR_LINEARITY, "name " + std::string(id) + " occurs more than twice");
+        w = mk_var(var_base + v);
+      } else {
+        const int lab = label_of(rules, id);
+        if (lab < 0) return fail(INET_ERR_PARSE, "unknown agent symbol " + std::string(id));
+        arity = rules.arity[(size_t)lab];
+        me = (uint32_t)out.nodes.size();
         Node nd;
-        nd.head = (int32_t)((uint32_t)li->second | (net_slot << 8));
+        nd.head = (int32_t)((uint32_t)lab | (net_slot << 8));
         nd.aux[0] = nd.aux[1] = nd.aux[2] = kEmpty;
         out.nodes.push_back(nd);
         w = mk_agent(agent_base + me);
-        int p = 0;
-        for (int k = s.first; k >= 0; k = syn[(size_t)k].next, p++) st.push_back({k, nullptr, (int64_t)me, p});
+        if (take('(')) {
+          if (!take(')')) opened = true;
+          else if (arity != 0) return fail(INET_ERR_PARSE, "wrong arity for " + std::string(id));
+        } else if (arity != 0) {
+          return fail(INET_ERR_PARSE, "wrong arity for " + std::string(id));
+        }
       }
-      if (it.parent >= 0) out.nodes[(size_t)it.parent].aux[it.port] = w;
-      else *it.dst = w;
+      if (frames.empty()) {
+        *w_out = w;
+      } else {
+        Frame& f = frames.back();
+        if (f.port >= f.arity) return fail(INET_ERR_PARSE, "wrong arity for an agent at offset " + std::to_string(p));
+        out.nodes[f.node].aux[f.port++] = w;
+      }
+      if (opened) {
+        frames.push_back({me, 0, arity});
+        continue;
+      }
+      for (;;) {
+        if (frames.empty()) return true;
+        if (take(',')) break;
+        if (!bad_char()) return false;
+        if (!take(')')) return fail_at("')' or ','");
+        const Frame& f = frames.back();
+        if (f.port != f.arity) return fail(INET_ERR_PARSE, "wrong arity for an agent before offset " + std::to_string(p));
+        frames.pop_back();
+      }
     }
-    return 0;
-  };
-  out.iface.resize(iface.size());
-  for (size_t i = 0; i < iface.size(); i++) {
-    int rc = build(iface[i], &out.iface[i]);
-    if (rc) return rc;
   }
-  // equations: ->com on the staged slots (second arrival takes the value)
-  for (auto& q : eqs) {
-    uint32_t t, u;
-    int rc = build(q.first, &t);
-    if (!rc) rc = build(q.second, &u);
-    if (rc) return rc;
-    for (int guard = 0;; guard++) {
-      if (guard > (int)out.vars.size() + 2) { err = "internal: link loop"; return INET_ERR_PARSE; }
-      if (is_agent(t) && is_agent(u)) { out.pairs.push_back({idx_of(t), idx_of(u)}); break; }
+
+  // ->com on the staged slots: the second arrival takes the value
+  bool link(uint32_t t, uint32_t u) {
+    for (size_t guard = 0;; guard++) {
+      if (guard > out.vars.size() + 2) return fail(INET_ERR_PARSE, "internal: link loop");
+      if (is_agent(t) && is_agent(u)) {
+        out.pairs.push_back({idx_of(t), idx_of(u)});
+        return true;
+      }
       if (!is_var(t)) std::swap(t, u);
       uint32_t& cell = out.vars[idx_of(t) - var_base];
-      uint32_t old = cell;
+      const uint32_t old = cell;
       cell = u;
-      if (old == kEmpty) break;
+      if (old == kEmpty) return true;
       cell = kEmpty;  // both top-level occurrences met: the slot is done
       t = old;
     }
   }
+
+  bool net() {
+    if (!bad_char()) return false;
+    if (!take('<')) return fail_at("'<'");
+    if (!take('|')) {
+      for (;;) {
+        uint32_t w = kEmpty;
+        if (!term(&w)) return false;
+        out.iface.push_back(w);
+        if (take('|')) break;
+        if (!bad_char()) return false;
+        if (!take(',')) return fail_at("',' or '|'");
+      }
+    }
+    if (!take('>')) {
+      for (;;) {
+        uint32_t t = kEmpty, u = kEmpty;
+        if (!term(&t)) return false;
+        if (!bad_char()) return false;
+        if (!take('=')) return fail_at("'='");
+        if (!term(&u)) return false;
+        if (!link(t, u)) return false;
+        if (take('>')) break;
+        if (!bad_char()) return false;
+        if (!take(',')) return fail_at("',' or '>'");
+      }
+    }
+    if (!bad_char()) return false;
+    if (peek()) return fail(INET_ERR_PARSE, "text after the end of the net");
+    if ((uint64_t)var_base + out.vars.size() > kMaxIndex || (uint64_t)agent_base + out.nodes.size() > kMaxIndex)
+      return fail(INET_ERR_ARENA_FULL, "net does not fit the index range");
+    return true;
+  }
+};
+
+}  // namespace
+
+int flatten_net(const std::string& text, const CompiledRules& rules, uint32_t net_slot,
+                uint32_t agent_base, uint32_t var_base, FlatNet& out, std::string& err) {
+  out = FlatNet();
+  NetReader rd{text, rules, net_slot, agent_base, var_base, out, err};
+  if (!rd.net()) return rd.rc ? rd.rc : INET_ERR_PARSE;
   return 0;
 }
 

@@ -90,6 +90,19 @@ def test_rule_errors(capi, text, status):
     ("< r | Add(y r) = Z >", "PARSE"),
     ("< r | Add(y, r) = Z", "PARSE"),
     ("< r | Add(y, r) = Z > junk", "PARSE"),
+    ("< r | S(r >", "PARSE"),
+    ("< r | S(r)) = Z >", "PARSE"),
+    ("< r | S(Z, Z) = r >", "PARSE"),
+    ("< r | S = r >", "PARSE"),
+    ("< r | S() = r >", "PARSE"),
+    ("< r | r = Z > $", "PARSE"),
+    ("< r | r = Z $ >", "PARSE"),
+    ("< r | r -> Z >", "PARSE"),
+    ("< r | r(x) = Z, x = Z >", "PARSE"),
+    ("< r | r = Z, >", "PARSE"),
+    ("", "PARSE"),
+    ("r = Z", "PARSE"),
+    ("< x, x, x | >", "LINEARITY"),
 ])
 def test_net_errors(capi, text, status):
     ctx = host_ctx(capi)
@@ -97,6 +110,23 @@ def test_net_errors(capi, text, status):
     with pytest.raises(capi.InetError) as e:
         capi.inet_load_net(ctx, text)
     assert e.value.name == status
+    capi.inet_destroy(ctx)
+
+
+@pytest.mark.parametrize("text,pairs", [
+    ("<r|Add(y,r)=S(Z),y=Z>", 1),
+    ("< r | # a comment to the end of the line\n  Add(y, r) = S(Z()) , y = Z() >", 1),
+    ("< | >", 0),
+    ("< r, s | r = s >", 0),
+    ("< S(Z), Z | >", 0),
+    ("< r | Add(y, r) = x, x = S(Z), y = Z >", 1),
+    ("< r | x = S(Z), Add(y, r) = x, y = Z >", 1),
+])
+def test_net_syntax_accepted(capi, text, pairs):
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    i = capi.inet_load_net(ctx, text)
+    assert capi.inet_net_info(ctx, i)["pending_pairs"] == pairs
     capi.inet_destroy(ctx)
 
 
