@@ -91,8 +91,9 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "6ddd982c9ffd"): 11_791_360 + 21_870_080,
-               ("lsys27", "persistent", "6ddd982c9ffd"): 4_345_088 + 3_790_080}
+NCU_TRAFFIC = {("mul2048", "async", "762d2a2d6ab0"): 11_711_488 + 24_415_744,
+               ("mul2048", "persistent", "762d2a2d6ab0"): 11_591_424 + 25_607_936,
+               ("lsys27", "persistent", "762d2a2d6ab0"): 4_341_504 + 3_718_912}
 
 
 def kernel_source_hash() -> str:

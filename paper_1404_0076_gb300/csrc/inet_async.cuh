@@ -544,21 +544,21 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
     }
     const uint32_t extra = np > 1 ? np - 1 : 0u;
     // pairs in flight: each new pair beyond a lane's own next one joins
-    // before it is published (lane 0 waits until the increment is performed,
-    // so no consumer's decrement can overtake it); each pair that produced
-    // nothing leaves afterwards.  At most cap pairs may be in flight, the
-    // capacity of the frontier that a stop drains them to; beyond it the
-    // arena is full.  Under that bound the queue slot a producer needs is
-    // held by a claimed ticket whenever it is still occupied: an unclaimed
-    // one would put every later ticket, and so more than cap pairs, in flight.
+    // before it is published to another warp (lane 0 waits until the
+    // increment is performed, so no consumer's decrement can overtake it);
+    // each pair that produced nothing leaves afterwards.  When every new
+    // pair stays in this warp the increment need not be waited for: only
+    // this warp's lane 0 can later count those pairs out, and its atomics on
+    // the counter are performed in program order, while the producing
+    // lane's own next pair keeps the count above zero meanwhile.  At most
+    // cap pairs may be in flight, the capacity of the frontier that a stop
+    // drains them to; beyond it the arena is full (checked whenever pairs
+    // go to the queue).  Under that bound the queue slot a producer needs
+    // is held by a claimed ticket whenever it is still occupied: an
+    // unclaimed one would put every later ticket, and so more than cap
+    // pairs, in flight.
     const long long grow = (long long)__reduce_add_sync(kFull, extra);
     const long long shrink = -(long long)__reduce_add_sync(kFull, had && np == 0 ? 1u : 0u);
-    if (lane == 0 && grow) {
-      const long long r =
-          (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&c->inflight), (unsigned long long)grow);
-      if (r + grow > (long long)cap) set_error(c, INET_ERR_ARENA_FULL, 9);
-    }
-    __syncwarp();
     if (grow) {
       // extra pairs go first to idle lanes of this warp (through shared
       // memory), the rest to the ticket queue
@@ -575,6 +575,16 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
         const unsigned nidle = __popc(idle);
         __syncwarp();
         const unsigned local = min(nidle, totx);
+        if (lane == 0) {
+          unsigned long long* ifl = reinterpret_cast<unsigned long long*>(&c->inflight);
+          if (totx > local) {
+            const long long r = (long long)atomicAdd(ifl, (unsigned long long)grow);
+            if (r + grow > (long long)cap) set_error(c, INET_ERR_ARENA_FULL, 9);
+          } else {
+            atomicAdd(ifl, (unsigned long long)grow);
+          }
+        }
+        __syncwarp();
         if ((idle >> lane) & 1u) {
           const unsigned r = __popc(idle & lanemask_lt());
           if (r < local) {

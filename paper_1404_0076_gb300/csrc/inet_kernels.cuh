@@ -992,38 +992,6 @@ __global__ void __launch_bounds__(512) k_persistent(Dev d) {
   flush_hist(d, s);
 }
 
-// Numeral readback of many nets, one thread per net: from the interface
-// word, follow name slots that hold a term (->col / ->sub) and count S
-// agents down to Z.  out[i] = k, or ~0 when the interface is not S^k(Z).
-__global__ void k_read_nats(Dev d, const uint32_t* roots, uint32_t n, int s_label, int z_label,
-                            unsigned long long* out) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  unsigned long long k = 0, res = ~0ull;
-  uint32_t w = roots[i];
-  for (unsigned long long guard = 0; guard <= d.cap_agents + d.cap_vars; guard++) {
-    if (is_var(w)) {
-      const uint32_t x = idx_of(w);
-      if (x >= d.cap_vars) break;
-      const uint32_t v = __ldcg(d.var + x);
-      if (v == kEmpty) break;
-      w = v;
-      continue;
-    }
-    if (!is_agent(w) || idx_of(w) >= d.cap_agents) break;
-    const int4 r = ld_node(d.node + idx_of(w));
-    const int lab = r.x & 0xFF;
-    if (lab == z_label) {
-      res = k;
-      break;
-    }
-    if (lab != s_label) break;
-    k++;
-    w = (uint32_t)r.y;
-  }
-  out[i] = res;
-}
-
 // Nets whose pending pairs reached zero and that were not reported before:
 // their ids go to out[0 .. cap) and they are marked reported (nets that do
 // not fit are left for the next call).  Runs between reductions.
