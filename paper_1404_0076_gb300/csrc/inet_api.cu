@@ -27,7 +27,8 @@ namespace {
 
 constexpr uint32_t kTraceCap = 1u << 20;
 constexpr uint32_t kReadChunk = 1u << 16;  // nets per device walk of inet_readback_nats
-constexpr uint32_t kWalkBudget = 128;      // elements one thread walks before the arena is ranked
+constexpr uint32_t kWalkMin = 128;         // elements one thread walks at least before the arena is ranked
+constexpr uint32_t kWalkMax = 1u << 20;
 constexpr uint64_t kDefaultAgents = 1ull << 22;
 constexpr uint64_t kDefaultVars = 1ull << 22;
 constexpr uint64_t kDefaultPairs = 1ull << 21;
@@ -332,13 +333,13 @@ inet_status ensure_net_counters(inet_ctx* ctx) {
 }
 
 // Numerals of m nets whose interface words are at droot, into dval, queued
-// on stream st: a walk of kWalkBudget elements per net, then list ranking of
+// on stream st: a bounded walk per net, then list ranking of
 // the whole arena when some walk ran out (inet_readback.cuh).  The arena is
 // quiescent for these nets (finished), so the slots below the host bump
 // counters hold every element of their lists.  No readback may be in
 // flight when the scratch grows.
 inet_status read_nats_device(inet_ctx* ctx, cudaStream_t st, const uint32_t* droot, uint32_t m, int s_label,
-                             int z_label, unsigned long long* dval) {
+                             int z_label, unsigned long long* dval, double rank_weight) {
   const uint32_t na = (uint32_t)ctx->a_bump, nv = (uint32_t)ctx->v_bump;
   const uint64_t n_slots = (uint64_t)na + nv;
   if (!ctx->jump_ctl) CK(cudaMalloc(&ctx->jump_ctl, sizeof(uint32_t) * kJumpCtl));
@@ -355,7 +356,21 @@ inet_status read_nats_device(inet_ctx* ctx, cudaStream_t st, const uint32_t* dro
   uint2* b1 = ctx->jump_buf + ctx->jump_cap;
   CK(cudaMemsetAsync(ctx->jump_ctl, 0, sizeof(uint32_t) * kJumpCtl, st));
   const unsigned nb = (m + 255) / 256;
-  k_nat_walk<<<nb, 256, 0, st>>>(ctx->dev, droot, m, na, nv, s_label, z_label, kWalkBudget, dval, ctx->jump_ctl);
+  // The walk's budget, as in ski rental: keep walking while the walk costs
+  // less than ranking would (about 0.75 us per element of the longest
+  // numeral against about 4 ps per slot of the arena and round, plus a few
+  // microseconds per round, at least log2(budget) rounds), so the two
+  // together cost at most about twice the cheaper one.  rank_weight scales
+  // the ranking's cost: below 1 when the caller waits and the GPU has
+  // nothing else to do, 1 when reductions run beside the readback and the
+  // ranking's traffic slows them.  A small arena is ranked after kWalkMin
+  // elements; a large one (a serving arena) is walked further.
+  uint32_t budget = kWalkMin;
+  for (uint32_t lg = 7; budget < kWalkMax; budget *= 2, lg++) {
+    const double walk_s = 0.75e-6 * budget, rank_s = rank_weight * lg * (4e-12 * (double)n_slots + 5e-6);
+    if (walk_s >= rank_s) break;
+  }
+  k_nat_walk<<<nb, 256, 0, st>>>(ctx->dev, droot, m, na, nv, s_label, z_label, budget, dval, ctx->jump_ctl);
   CK(cudaGetLastError());
   if (n_slots == 0) return INET_OK;
   const unsigned grid =
@@ -1188,7 +1203,7 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
     uint32_t* droot = at<uint32_t>(ctx, ctx->lay.rb_root);
     unsigned long long* dval = at<unsigned long long>(ctx, ctx->lay.rb_val);
     CK(h2d(ctx, droot, roots.data() + off, sizeof(uint32_t) * (size_t)m));
-    if ((s = read_nats_device(ctx, ctx->stream, droot, (uint32_t)m, si->second, zi->second, dval))) return s;
+    if ((s = read_nats_device(ctx, ctx->stream, droot, (uint32_t)m, si->second, zi->second, dval, 0.25))) return s;
     CK(d2h(ctx, values_out + off, dval, sizeof(unsigned long long) * (size_t)m));
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1232,7 +1247,7 @@ inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int3
     CK(cudaStreamWaitEvent(ctx->rb_stream, ctx->rb_after, 0));
     CK(cudaMemcpyAsync(droot, ctx->rb_host_roots, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
                        ctx->rb_stream));
-    if ((s = read_nats_device(ctx, ctx->rb_stream, droot, (uint32_t)n, si->second, zi->second, dval))) return s;
+    if ((s = read_nats_device(ctx, ctx->rb_stream, droot, (uint32_t)n, si->second, zi->second, dval, 1.0))) return s;
     CK(cudaMemcpyAsync(ctx->rb_host_vals, dval, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToHost,
                        ctx->rb_stream));
     CK(cudaEventRecord(ctx->rb_ready, ctx->rb_stream));
