@@ -91,9 +91,9 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "762d2a2d6ab0"): 11_711_488 + 24_415_744,
-               ("mul2048", "persistent", "762d2a2d6ab0"): 11_591_424 + 25_607_936,
-               ("lsys27", "persistent", "762d2a2d6ab0"): 4_341_504 + 3_718_912}
+NCU_TRAFFIC = {("mul2048", "async", "849202111aca"): 11_783_680 + 23_814_912,
+               ("mul2048", "persistent", "849202111aca"): 11_597_568 + 26_159_360,
+               ("lsys27", "persistent", "849202111aca"): 4_351_744 + 3_605_248}
 
 
 def kernel_source_hash() -> str:

@@ -237,6 +237,9 @@ void fill_dev(inet_ctx* ctx) {
   d.eq = nullptr;
   d.eq_n = nullptr;
   d.cap_eq = 0;
+  d.eq_fix = nullptr;
+  d.eq_fix_n = 0;
+  d.cap_fix = 0;
   d.cond = 0;
 }
 
@@ -904,17 +907,27 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
     const uint64_t cap_eq64 = std::min<uint64_t>(2 * ctx->cfg.max_vars + 1024, 0x7FFFFF00ull);
     const uint32_t cap_eq = (uint32_t)cap_eq64;
     const uint32_t tiles_max = (cap_eq + kRsTile - 1) / kRsTile;
+    // n result slots per active pair (Sec. 3.4): the most equations of any
+    // right-hand side
+    uint32_t nfix = 1;
+    for (const Template& t : ctx->rules.tmpl) nfix = std::max<uint32_t>(nfix, t.n_link);
+    const uint64_t cap_fix = (uint64_t)ctx->cfg.max_pairs * nfix;
+    const uint32_t fix_tiles_max = (uint32_t)((cap_fix + kCpTile - 1) / kCpTile);
     CtlBufs bufs;
-    unsigned long long *eq = nullptr, *v0 = nullptr, *v1 = nullptr;
-    uint32_t *k0 = nullptr, *k1 = nullptr, *counts = nullptr, *pc = nullptr;
+    unsigned long long *eq = nullptr, *v0 = nullptr, *v1 = nullptr, *fix = nullptr;
+    uint32_t *k0 = nullptr, *k1 = nullptr, *counts = nullptr, *pc = nullptr, *fcounts = nullptr;
     if (!bufs.get(&eq, cap_eq) || !bufs.get(&v0, cap_eq) || !bufs.get(&v1, cap_eq) || !bufs.get(&k0, cap_eq) ||
-        !bufs.get(&k1, cap_eq) || !bufs.get(&counts, (size_t)256 * tiles_max) || !bufs.get(&pc, 4))
+        !bufs.get(&k1, cap_eq) || !bufs.get(&counts, (size_t)256 * tiles_max) || !bufs.get(&pc, 4) ||
+        !bufs.get(&fix, (size_t)cap_fix) || !bufs.get(&fcounts, fix_tiles_max))
       return fail(ctx, INET_ERR_CUDA, "no device memory for the equation arrays of the paper's form");
     Dev dp = d;
     dp.paper = 1;
     dp.eq = eq;
     dp.eq_n = pc;
     dp.cap_eq = cap_eq;
+    dp.eq_fix = fix;
+    dp.eq_fix_n = nfix;
+    dp.cap_fix = cap_fix;
     CK(cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), ctx->stream));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));  // the arrays are set up outside the measured time
     const uint64_t nv = ctx->v_bump;
@@ -927,7 +940,14 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
         k_paper_prep<<<1, 1, 0, ctx->stream>>>(dp);
         const uint32_t grid = std::max<uint32_t>(1, (pending + (uint32_t)B - 1) / (uint32_t)B);
         k_step<<<grid, B, smem, ctx->stream>>>(dp);
-        launches += 2;
+        // the dummies out, the equations after those already in the array
+        const uint64_t mf = (uint64_t)pending * nfix;
+        const uint32_t ft = (uint32_t)((mf + kCpTile - 1) / kCpTile);
+        k_paper_compact_count<<<ft, kCpThreads, 0, ctx->stream>>>(fix, mf, fcounts);
+        k_rs_scan<<<1, 1024, 0, ctx->stream>>>(fcounts, ft);
+        k_paper_compact_scatter<<<ft, kCpThreads, 0, ctx->stream>>>(dp, fix, mf, fcounts, pc + 2);
+        k_paper_compact_done<<<1, 1, 0, ctx->stream>>>(dp, pc + 2);
+        launches += 6;
       }
       CK(cudaMemsetAsync(pc + 1, 0, sizeof(uint32_t), ctx->stream));
       uint32_t m = 0;

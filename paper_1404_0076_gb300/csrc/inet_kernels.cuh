@@ -85,10 +85,13 @@ struct Dev {
   unsigned long long* netctr;
   int32_t* netstat;
   uint32_t* netrep;      // 1 once inet_net_finished reported the net
-  uint32_t paper;        // the paper's loop form: name equations go to `eq` instead of being linked
-  unsigned long long* eq;  // equations t | u << 32 of the paper's form
+  uint32_t paper;        // the paper's loop form: name equations go to `eq_fix` instead of being linked
+  unsigned long long* eq;  // equations t | u << 32 of the paper's form (communication phase)
   uint32_t* eq_n;
   uint32_t cap_eq;
+  unsigned long long* eq_fix;  // interaction phase of the paper's form: eq_fix_n result slots per pair
+  uint32_t eq_fix_n;
+  unsigned long long cap_fix;
   unsigned long long* rule_hist;
   Ctrl* ctrl;
   const int16_t* table;
@@ -343,7 +346,8 @@ __device__ __forceinline__ uint32_t pool_slot(const uint32_t* ring, unsigned lon
 // which resolves chains x1 = x2 = .. of any length in one call (the chains of
 // Sec. 3.6 that need several passes of the sorting algorithm).  Returns true
 // and the pair when an active pair results.
-__device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t, uint32_t u, Pair* out) {
+__device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t, uint32_t u, Pair* out,
+                                        unsigned long long slot) {
   for (uint32_t guard = 0;; guard++) {
     if (is_agent(t) && is_agent(u)) {
       out->a = idx_of(t);
@@ -351,9 +355,9 @@ __device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t,
       return true;
     }
     if (d.paper) {
-      // the paper's form: the equation waits for the communication phase
-      const uint32_t k = atomicAdd(d.eq_n, 1u);
-      if (k < d.cap_eq) d.eq[k] = (unsigned long long)t | ((unsigned long long)u << 32);
+      // the paper's form (Sec. 3.4): the equation goes to its result slot
+      // and waits for the communication phase
+      if (slot < d.cap_fix) d.eq_fix[slot] = (unsigned long long)t | ((unsigned long long)u << 32);
       else set_error(d.ctrl, INET_ERR_ARENA_FULL, 26);
       return false;
     }
@@ -558,10 +562,16 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
   // global reservation per block).
   uint32_t pushed = 0;
   const uint32_t max_link = __reduce_max_sync(kFull, n_link);
+  // the paper's form (Sec. 3.4): every pair of the step owns eq_fix_n result
+  // slots; those its name equations do not fill stay dummies (0)
+  const unsigned long long slot0 = (unsigned long long)i * d.eq_fix_n;
+  if (d.paper && i < n)
+    for (uint32_t k = 0; k < d.eq_fix_n; k++)
+      if (slot0 + k < d.cap_fix) d.eq_fix[slot0 + k] = 0ull;
   for (uint32_t k = 0; k < max_link; k++) {
     Pair out;
     bool has = false;
-    if (k < n_link) has = link_eq(d, s, vals[T.link[k][0] * B], vals[T.link[k][1] * B], &out);
+    if (k < n_link) has = link_eq(d, s, vals[T.link[k][0] * B], vals[T.link[k][1] * B], &out, slot0 + k);
     const unsigned m = __ballot_sync(kFull, has);
     if (m) {
       const int leader = __ffs(m) - 1;

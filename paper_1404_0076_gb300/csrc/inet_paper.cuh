@@ -1,11 +1,15 @@
 // The paper's own loop form (Sec. 3.6, evaluate()): an interaction phase,
 // then one communication phase, repeated until neither an interaction nor a
-// communication happened.  The interaction phase is the step kernel with
-// the name equations of each right-hand side written to an equation array
-// instead of being linked (agent = agent equations are active pairs at
-// once); the communication phase is Sec. 3.5: all name-headed equations are
-// sorted by the name (stable LSD radix sort, inet_control.cuh) and adjacent
-// equations x = t, x = s are folded into s = t, one ->com per name and pass.
+// communication happened.  The interaction phase is Sec. 3.4: the step
+// kernel gives every active pair a fixed number n of result slots (n = the
+// most equations any right-hand side has), writes the pair's name equations
+// there instead of linking them and leaves the other slots as dummies
+// (agent = agent equations are active pairs at once); the dummies are then
+// removed by a stable stream compaction that appends the equations to the
+// equation array.  The communication phase is Sec. 3.5: all name-headed
+// equations are sorted by the name (stable LSD radix sort,
+// inet_control.cuh) and adjacent equations x = t, x = s are folded into
+// s = t, one ->com per name and pass.
 // While this form runs, name bindings live in the equation array only: the
 // bindings already in name slots are collected into it first, and what is
 // left at the end is deposited back, so any loop form can continue.
@@ -15,6 +19,71 @@
 #include "inet_kernels.cuh"
 
 namespace inet {
+
+constexpr int kCpThreads = 256;
+constexpr int kCpItems = 16;                     // consecutive slots per thread
+constexpr int kCpTile = kCpThreads * kCpItems;   // 4096 slots per block
+
+// Removal of the dummies (Sec. 3.4), step 1: non-dummy slots per tile.
+__global__ void __launch_bounds__(kCpThreads) k_paper_compact_count(const unsigned long long* fix,
+                                                                    unsigned long long m, uint32_t* counts) {
+  __shared__ uint32_t wsum[kCpThreads / 32];
+  const unsigned long long base = (unsigned long long)blockIdx.x * kCpTile + (unsigned long long)threadIdx.x * kCpItems;
+  uint32_t c = 0;
+  for (int r = 0; r < kCpItems; r++)
+    if (base + r < m && fix[base + r]) c++;
+  c = __reduce_add_sync(0xFFFFFFFFu, c);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kCpThreads / 32; w++) t += wsum[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// Step 2 (after an exclusive scan of the tile counts): each tile writes its
+// equations, in slot order, after the equations already in the array
+// (*d.eq_n of them); the last tile leaves the total in *total.
+__global__ void __launch_bounds__(kCpThreads) k_paper_compact_scatter(Dev d, const unsigned long long* fix,
+                                                                      unsigned long long m, const uint32_t* offsets,
+                                                                      uint32_t* total) {
+  __shared__ uint32_t wsum[kCpThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned long long base = (unsigned long long)blockIdx.x * kCpTile + (unsigned long long)threadIdx.x * kCpItems;
+  uint32_t c = 0;
+  for (int r = 0; r < kCpItems; r++)
+    if (base + r < m && fix[base + r]) c++;
+  // exclusive prefix of c over the block: within the warp, then the warps
+  uint32_t inc = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+  for (int w = 0; w < kCpThreads / 32; w++) {
+    if (w < wid) before += wsum[w];
+    all += wsum[w];
+  }
+  const uint32_t e0 = __ldcg(d.eq_n);
+  uint32_t at = e0 + offsets[blockIdx.x] + before + inc - c;
+  for (int r = 0; r < kCpItems; r++) {
+    if (base + r >= m) break;
+    const unsigned long long v = fix[base + r];
+    if (!v) continue;
+    if (at < d.cap_eq) d.eq[at] = v;
+    else set_error(d.ctrl, INET_ERR_ARENA_FULL, 27);
+    at++;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = offsets[blockIdx.x] + all;
+}
+
+// Step 3: the equation count grows by the compacted total.
+__global__ void k_paper_compact_done(Dev d, const uint32_t* total) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d.eq_n += *total;
+}
 
 // Before a paper-form reduction: every bound name slot becomes an equation
 // x = value and the slot is cleared.
