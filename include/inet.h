@@ -80,14 +80,18 @@ enum {
                                independent, Sec. 2.1); no per-step trace; more
                                than max_pairs pairs in flight at once is
                                INET_ERR_ARENA_FULL */
-  INET_MODE_PAPER = 4       /* the paper's own loop (Sec. 3.6): each step's name
-                               equations are collected, then one communication
-                               pass sorts them by name and folds adjacent pairs
+  INET_MODE_PAPER = 4       /* the paper's own loop (Sec. 3.6): each step writes
+                               the name equations of every active pair to n
+                               result slots of its own, dummies in the rest,
+                               and a stream compaction removes the dummies
+                               (Sec. 3.4); then one communication pass sorts
+                               the equations by name and folds adjacent pairs
                                (Sec. 3.5), until neither produced anything; for
                                comparison.  Runs to the end (max_steps and
                                slice_us are ignored); needs 2 * max_vars
-                               equations of scratch (36 bytes each, allocated per
-                               call); freed names return to the ring */
+                               equations of scratch (36 bytes each) and n
+                               slots of 8 bytes per frontier pair, allocated
+                               per call; freed names return to the ring */
 };
 
 typedef struct inet_reduce_opts {
