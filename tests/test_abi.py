@@ -246,3 +246,70 @@ def test_reduce_refuses_bad_modes_and_shapes(capi):
     for mode, block in ((9, 256), (capi.INET_MODE_ASYNC, 512), (capi.INET_MODE_PAPER, 16)):
         st, _ = capi.inet_reduce(ctx, [i], capi.inet_reduce_opts(mode, block, 0, 0, 0, 0, 0, 0), check=False)
         assert st in (capi.INET_ERR_INVALID_ARG, capi.INET_ERR_NO_DEVICE)
+
+
+def _loaded_pairs(capi, ctx, ids):
+    return [capi.inet_net_info(ctx, i)["pending_pairs"] for i in ids]
+
+
+def test_batch_loads_from_several_threads_at_once(capi):
+    # the host pool runs one job at a time; a second caller parses on its
+    # own thread, and every context gets the same nets as a lone load
+    import threading
+    nets = W.config1(count=700).nets
+    ref = host_ctx(capi)
+    capi.inet_load_rules(ref, W.ARITH_RULES)
+    want = _loaded_pairs(capi, ref, capi.inet_load_nets(ref, nets))
+    ctxs = [host_ctx(capi) for _ in range(4)]
+    out = [None] * len(ctxs)
+
+    def work(k):
+        capi.inet_load_rules(ctxs[k], W.ARITH_RULES)
+        for _ in range(3):
+            capi.inet_reset(ctxs[k])
+            ids = capi.inet_load_nets(ctxs[k], nets)
+        out[k] = _loaded_pairs(capi, ctxs[k], ids)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(len(ctxs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=120)
+    assert all(o == want for o in out)
+    for c in ctxs + [ref]:
+        capi.inet_destroy(c)
+
+
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")  # forking a threaded process is the point
+def test_batch_load_in_a_forked_child(capi):
+    # a process forked after the pool started has no pool threads: the
+    # child must load on its own thread instead of waiting for them
+    import time
+    nets = W.config1(count=300).nets
+    ctx = host_ctx(capi)
+    capi.inet_load_rules(ctx, W.ARITH_RULES)
+    capi.inet_load_nets(ctx, nets)  # the pool is running now
+    pid = os.fork()
+    if pid == 0:
+        code = 1
+        try:
+            c2 = host_ctx(capi)
+            capi.inet_load_rules(c2, W.ARITH_RULES)
+            ids = capi.inet_load_nets(c2, nets)
+            code = 0 if len(ids) == len(nets) else 2
+        finally:
+            os._exit(code)
+    deadline = time.time() + 60
+    status = None
+    while time.time() < deadline:
+        done, st = os.waitpid(pid, os.WNOHANG)
+        if done:
+            status = st
+            break
+        time.sleep(0.05)
+    if status is None:
+        os.kill(pid, 9)
+        os.waitpid(pid, 0)
+    capi.inet_destroy(ctx)
+    assert status is not None, "the forked child did not finish its load"
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
