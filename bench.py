@@ -405,10 +405,26 @@ def main():
     prepared()
     stp_depth = ev.reduce([], mode="persistent")
     depth = stp_depth["steps"]
+    # the latency of one interaction with nothing else running: one warp on
+    # one dependent chain of Add interactions (arithmetic rule set only)
+    lone = None
+    if rules_text == W.ARITH_RULES:
+        ev.reset()
+        ids_c = ev.load_nets([W.add_net(20000, 0)])
+        ev.stage(ids_c)
+        torch.cuda.synchronize()
+        stc = ev.reduce([], mode="async", block=32, grid=1)
+        lone = 1e6 * stc["device_ms"] / max(1, stc["interactions"])
+    step_s = total_s / args.steps
     roof["critical_path"] = {"depth_steps": depth,
-                             "ns_per_level": 1e9 * (total_s / args.steps) / max(1, depth),
+                             "ns_per_level": 1e9 * step_s / max(1, depth),
+                             "lone_chain_ns_per_interaction": lone,
+                             "bound_ms": depth * lone * 1e-6 if lone else None,
+                             "frac": depth * lone * 1e-9 / step_s if lone else None,
                              "how": "depth = steps of the maximally parallel loop (persistent form) on the same batch; "
-                                    "ns_per_level = timed device time per step / depth"}
+                                    "ns_per_level = timed device time per step / depth; lone chain = one warp "
+                                    "reducing Add(Z, r) = S^20000 Z with nothing else running; bound = depth x that "
+                                    "latency, the time if every level of the batch ran at it"}
 
     # e2e: public API from host text to host results, copies included
     e2e_ms, e2e_h2d, e2e_d2h, e2e_int = [], 0, 0, 0
