@@ -87,8 +87,7 @@ class InetError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
-                          "or python -m paper_1404_0076_gb300.build")
+        raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_1404_0076_gb300.build")
     lib = C.CDLL(LIB_PATH)
     P = C.c_void_p
     sig = {
