@@ -98,7 +98,8 @@ typedef struct inet_reduce_opts {
   int32_t mode;          /* INET_MODE_* */
   int32_t block;         /* threads per block, multiple of 32 in [64, 512] (ASYNC: [32, 256]); 0 = 256 */
   int32_t grid;          /* blocks for GRAPH / PERSISTENT / ASYNC; 0 = automatic
-                            (ASYNC: one block per SM) */
+                            (ASYNC and PERSISTENT: as many as can be resident,
+                            full occupancy) */
   int32_t solo_max;      /* PERSISTENT: frontier sizes <= solo_max run on block 0
                             alone; 0 = automatic, < 0 = never */
   uint64_t max_steps;    /* stop after this many steps of this call (0 = no limit);

@@ -39,7 +39,7 @@ def candidates(mode: str, num_sms: int) -> list[dict]:
                 [dict(mode="persistent", **s) for s in candidates("persistent", num_sms)])
     if mode == "async":
         return [dict(block=b, grid=g) for b in (64, 128, 256)
-                for g in (num_sms // 2, num_sms, 2 * num_sms, 4 * num_sms)]
+                for g in (num_sms // 2, num_sms, 2 * num_sms, 4 * num_sms, 8 * num_sms)]
     if mode == "persistent":
         return [dict(block=b, grid=0, solo_max=s) for b in (128, 256, 512) for s in (0, 1024, -1)]
     if mode in ("graph", "plain"):

@@ -874,7 +874,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async, B, smem_a));
     const int maxg = std::max(1, per) * ctx->num_sms;
     // default: one block per SM (more warps mostly add idle polling)
-    const int grid = o.grid > 0 ? std::min(o.grid, maxg) : std::min(maxg, ctx->num_sms);
+    const int grid = o.grid > 0 ? std::min(o.grid, maxg) : maxg;
     if (o.slice_us > 0) d.slice_ns = (unsigned long long)o.slice_us * 1000ull;
     uint32_t q = cur;
     for (;;) {

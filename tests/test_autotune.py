@@ -36,7 +36,7 @@ def test_candidates_cover_each_form():
     for mode in ("async", "persistent", "graph", "plain"):
         c = candidates(mode, 152)
         assert c and all(s["block"] % 32 == 0 for s in c)
-    assert {s["grid"] for s in candidates("async", 152)} == {76, 152, 304, 608}
+    assert {s["grid"] for s in candidates("async", 152)} == {76, 152, 304, 608, 1216}
     with pytest.raises(ValueError):
         candidates("warp", 152)
 
