@@ -91,9 +91,9 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "849202111aca"): 11_783_680 + 23_814_912,
-               ("mul2048", "persistent", "849202111aca"): 11_597_568 + 26_159_360,
-               ("lsys27", "persistent", "849202111aca"): 4_351_744 + 3_605_248}
+NCU_TRAFFIC = {("mul2048", "async", "f4e58a84a065"): 5_985_536 + 8_249_344,
+               ("mul2048", "persistent", "f4e58a84a065"): 11_581_184 + 25_868_288,
+               ("lsys27", "persistent", "f4e58a84a065"): 4_346_880 + 3_804_672}
 
 
 def kernel_source_hash() -> str:
