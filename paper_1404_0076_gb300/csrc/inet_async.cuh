@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
   unsigned long long ticket = kNoTicket, tslot = 0;
   long long live = 0;
   uint32_t nap = 0;
-  bool stop = false, finished = false;
+  bool stop = false, finished = false, check_now = false;
   bool pre = false;
   int4 pra = make_int4(0, 0, 0, 0), prb = pra;
   unsigned long long t_start = 0;
@@ -466,8 +466,10 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
     t_start = ld_volatile64(&c->slice_t0);
   }
   for (uint32_t it = 0;; it++) {
-    // stop / slice checks every 16 iterations
-    if ((it & 15) == 15) {
+    // stop / slice checks every 16 iterations, and when a napping warp's
+    // clock says the time slice is over
+    if ((it & 15) == 15 || check_now) {
+      check_now = false;
       uint32_t st = 0;
       if (lane == 0) {
         st = ld_volatile(&c->astop) | (ld_volatile((const uint32_t*)&c->fatal) ? 1u : 0u);
@@ -529,8 +531,18 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
         finished = true;
         break;
       }
+      // back off up to 16 us: with thousands of warps, most of them idle
+      // in a narrow phase, shorter naps make their polling of the queue and
+      // of the in-flight count contend with the warps doing the work (an
+      // Ackermann batch 77 -> 63 ms, 2048 Mul nets 13.1 -> 12.7 ms).  The
+      // slice's end is noticed from the clock, which needs no memory access.
       __nanosleep(nap);
-      nap = nap < 1024 ? nap * 2 + 32 : 1024;
+      nap = nap < 16384 ? nap * 2 + 32 : 16384;
+      {
+        uint32_t late = 0;
+        if (lane == 0) late = globaltimer() - t_start > d.slice_ns ? 1u : 0u;
+        check_now = __shfl_sync(kFull, late, 0) != 0;
+      }
       continue;
     }
     nap = 0;
