@@ -133,6 +133,13 @@ struct inet_ctx {
   bool h_net_valid = true;  // false: the device changed them since the last copy
   // readback snapshot
   bool snap_valid = false;
+  uint64_t snap_gen = 0;                    // counts snapshots taken
+  // the text of the last inet_readback, so that a size query followed by
+  // the copy walks the net once
+  int32_t text_net = -1;
+  uint64_t text_gen = 0;
+  std::string text;
+  uint64_t text_reached = 0;                // agents that walk reached
   std::vector<Node> snap_nodes;
   std::vector<uint32_t> snap_vars;
   std::vector<int64_t> snap_live;
@@ -469,6 +476,7 @@ inet_status ensure_snapshot(inet_ctx* ctx) {
     if (net < ctx->snap_live.size()) ctx->snap_live[net]++;
   }
   ctx->snap_valid = true;
+  ctx->snap_gen++;
   return INET_OK;
 }
 
@@ -1151,12 +1159,18 @@ inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, 
   if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx)) ||
       (s = ensure_net_counters(ctx)))
     return s;
-  Readback rb;
-  read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
-           ctx->nets[(size_t)net_id].iface, ctx->rules, (size_t)-1 / 2, true, rb);
-  if (needed_out) *needed_out = rb.text.size() + 1;
-  if (!buf || cap < rb.text.size() + 1) return fail(ctx, INET_ERR_INVALID_ARG, "buffer too small");
-  memcpy(buf, rb.text.c_str(), rb.text.size() + 1);
+  if (ctx->text_net != net_id || ctx->text_gen != ctx->snap_gen) {
+    Readback rb;
+    read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
+             ctx->nets[(size_t)net_id].iface, ctx->rules, (size_t)-1 / 2, true, rb);
+    ctx->text = std::move(rb.text);
+    ctx->text_reached = rb.reached;
+    ctx->text_net = net_id;
+    ctx->text_gen = ctx->snap_gen;
+  }
+  if (needed_out) *needed_out = ctx->text.size() + 1;
+  if (!buf || cap < ctx->text.size() + 1) return fail(ctx, INET_ERR_INVALID_ARG, "buffer too small");
+  memcpy(buf, ctx->text.c_str(), ctx->text.size() + 1);
   return INET_OK;
 }
 
@@ -1350,11 +1364,15 @@ inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out) {
   out->interactions = v & kNetIntMask;
   out->pending_pairs = v >> kNetPairShift;
   out->reduced = nr.started && out->pending_pairs == 0 ? 1 : 0;
-  Readback rb;
-  read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(), nr.iface,
-           ctx->rules, 0, false, rb);
+  uint64_t reached = ctx->text_reached;
+  if (ctx->text_net != net_id || ctx->text_gen != ctx->snap_gen) {  // no text walk of this snapshot to reuse
+    Readback rb;
+    read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(), nr.iface,
+             ctx->rules, 0, false, rb);
+    reached = rb.reached;
+  }
   out->live_agents = (size_t)net_id < ctx->snap_live.size() ? ctx->snap_live[(size_t)net_id] : 0;
-  out->residual_agents = out->live_agents - rb.reached;
+  out->residual_agents = out->live_agents - reached;
   return INET_OK;
 }
 
@@ -1390,6 +1408,8 @@ inet_status inet_reset(inet_ctx* ctx) {
   ctx->step = 0;
   ctx->fcount[0] = ctx->fcount[1] = 0;
   ctx->snap_valid = false;
+  ctx->text_net = -1;
+  std::string().swap(ctx->text);
   ctx->tr_front.clear();
   ctx->tr_live.clear();
   ctx->poisoned = false;

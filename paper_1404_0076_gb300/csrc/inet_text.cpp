@@ -571,6 +571,13 @@ void read_net(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_
     while (is_var(w) && idx_of(w) < n_vars && vars[idx_of(w)] != kEmpty && hops++ <= n_vars) w = vars[idx_of(w)];
     return w;
   };
+  // the walk visits agents in random order in a large snapshot: start the
+  // load of a child's record when it is pushed, so that most of them have
+  // arrived when it is popped
+  auto prefetch = [&](uint32_t w) {
+    if (is_agent(w) && idx_of(w) < n_nodes) __builtin_prefetch(nodes + idx_of(w));
+    else if (is_var(w) && idx_of(w) < n_vars) __builtin_prefetch(vars + idx_of(w));
+  };
   std::string& s = out.text;
   struct Item { uint32_t w; char emit; };  // emit != 0: literal ')' or ','
   for (size_t i = 0; i < iface.size(); i++) {
@@ -605,8 +612,12 @@ void read_net(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_
       if (ar == 0) continue;
       if (want_text) s += "(";
       st.push_back({0, ')'});
+      // the children's name slots are read here, independently of each
+      // other, and their records prefetched
       for (int k = ar - 1; k >= 0; k--) {
-        st.push_back({nodes[a].aux[k], 0});
+        const uint32_t cw = resolve(nodes[a].aux[k]);
+        prefetch(cw);
+        st.push_back({cw, 0});
         if (k) st.push_back({0, ','});
       }
     }
