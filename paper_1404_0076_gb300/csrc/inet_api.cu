@@ -1161,8 +1161,8 @@ inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, 
     return s;
   if (ctx->text_net != net_id || ctx->text_gen != ctx->snap_gen) {
     Readback rb;
-    read_net(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
-             ctx->nets[(size_t)net_id].iface, ctx->rules, (size_t)-1 / 2, true, rb);
+    read_net_text(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
+                  ctx->nets[(size_t)net_id].iface, ctx->rules, rb);
     ctx->text = std::move(rb.text);
     ctx->text_reached = rb.reached;
     ctx->text_net = net_id;

@@ -4,11 +4,15 @@
 #include "inet_text.h"
 
 #include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <cctype>
 #include <cstring>
 #include <string_view>
 #include <unordered_map>
 
+#include "host_pool.h"
 #include "inet.h"
 
 namespace inet {
@@ -559,6 +563,29 @@ int flatten_net(const std::string& text, const CompiledRules& rules, uint32_t ne
 // ---------------------------------------------------------------------------
 // Readback walk.
 
+// k when the interface is one numeral S^k(Z), else -1.
+static int64_t numeral_of(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_t n_vars,
+                          const std::vector<uint32_t>& iface, const CompiledRules& rules) {
+  auto si = rules.index.find("S");
+  auto zi = rules.index.find("Z");
+  if (iface.size() != 1 || si == rules.index.end() || zi == rules.index.end() ||
+      rules.arity[(size_t)si->second] != 1 || rules.arity[(size_t)zi->second] != 0)
+    return -1;
+  auto resolve = [&](uint32_t w) -> uint32_t {
+    uint64_t hops = 0;
+    while (is_var(w) && idx_of(w) < n_vars && vars[idx_of(w)] != kEmpty && hops++ <= n_vars) w = vars[idx_of(w)];
+    return w;
+  };
+  int64_t k = 0;
+  uint32_t w = resolve(iface[0]);
+  uint64_t guard = 0;
+  while (is_agent(w) && idx_of(w) < n_nodes && (nodes[idx_of(w)].head & 0xFF) == si->second && guard++ < n_nodes) {
+    k++;
+    w = resolve(nodes[idx_of(w)].aux[0]);
+  }
+  return is_agent(w) && idx_of(w) < n_nodes && (nodes[idx_of(w)].head & 0xFF) == zi->second ? k : -1;
+}
+
 void read_net(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_t n_vars,
               const std::vector<uint32_t>& iface, const CompiledRules& rules, size_t max_chars,
               bool want_text, Readback& out) {
@@ -622,20 +649,170 @@ void read_net(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_
       }
     }
   }
-  // numeral S^k(Z)
-  auto si = rules.index.find("S");
-  auto zi = rules.index.find("Z");
-  if (iface.size() == 1 && si != rules.index.end() && zi != rules.index.end() &&
-      rules.arity[(size_t)si->second] == 1 && rules.arity[(size_t)zi->second] == 0) {
-    int64_t k = 0;
-    uint32_t w = resolve(iface[0]);
-    uint64_t guard = 0;
-    while (is_agent(w) && idx_of(w) < n_nodes && (nodes[idx_of(w)].head & 0xFF) == si->second && guard++ < n_nodes) {
-      k++;
-      w = resolve(nodes[idx_of(w)].aux[0]);
-    }
-    if (is_agent(w) && idx_of(w) < n_nodes && (nodes[idx_of(w)].head & 0xFF) == zi->second) out.nat = k;
+  out.nat = numeral_of(nodes, n_nodes, vars, n_vars, iface, rules);
+}
+
+// Text readback of a large net in parallel.  The forest of interface terms
+// is unfolded breadth-first from the roots until it has about 128 pending
+// subterms (or nothing is left to unfold); the pending subterms are then
+// rendered on the host pool, each by the depth-first walk of read_net, and
+// the pieces joined in order.  Names are rendered as placeholders (the
+// resolved word between two control bytes) and renamed x0, x1, .. in one
+// pass over the joined text, in order of first occurrence, as read_net
+// does, so the result is the same text.
+void read_net_text(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_t n_vars,
+                   const std::vector<uint32_t>& iface, const CompiledRules& rules, Readback& out) {
+  out = Readback();
+  auto resolve = [&](uint32_t w) -> uint32_t {
+    uint64_t hops = 0;
+    while (is_var(w) && idx_of(w) < n_vars && vars[idx_of(w)] != kEmpty && hops++ <= n_vars) w = vars[idx_of(w)];
+    return w;
+  };
+  auto label = [&](int lab) -> const std::string& {
+    static const std::string unknown = "?";
+    return lab < (int)rules.labels.size() ? rules.labels[(size_t)lab] : unknown;
+  };
+  auto arity = [&](int lab) { return lab < (int)rules.arity.size() ? rules.arity[(size_t)lab] : 0; };
+  constexpr char kOpen = '\x01', kClose = '\x02';  // around a name's word, rendered later
+  auto name_mark = [&](std::string& s, uint32_t w) {
+    char buf[16];
+    const int n = snprintf(buf, sizeof buf, "%c%08x%c", kOpen, w, kClose);
+    s.append(buf, (size_t)n);
+  };
+  // pieces in text order: literal text, or a subterm still to render
+  struct Piece {
+    bool sub;
+    uint32_t w;
+    std::string text;
+  };
+  std::vector<Piece> pieces;
+  for (size_t i = 0; i < iface.size(); i++) {
+    if (i) pieces.push_back({false, 0, ", "});
+    pieces.push_back({true, iface[i], std::string()});
   }
+  std::atomic<int64_t> reached{0};
+  std::atomic<bool> truncated{false}, exhausted{false};
+  constexpr size_t kSubs = 128;
+  for (int round = 0; round < 32; round++) {
+    size_t subs = 0;
+    for (const Piece& p : pieces) subs += p.sub ? 1 : 0;
+    if (subs == 0 || subs >= kSubs) break;
+    std::vector<Piece> next;
+    next.reserve(pieces.size() * 2);
+    for (Piece& p : pieces) {
+      if (!p.sub) {
+        next.push_back(std::move(p));
+        continue;
+      }
+      const uint32_t w = resolve(p.w);
+      if (!is_agent(w) || idx_of(w) >= n_nodes) {
+        if (!is_agent(w)) {
+          Piece t{false, 0, std::string()};
+          name_mark(t.text, w);
+          next.push_back(std::move(t));
+        } else {
+          truncated = true;
+        }
+        continue;
+      }
+      const Node& nd = nodes[idx_of(w)];
+      reached++;
+      const int lab = nd.head & 0xFF, ar = arity(lab);
+      next.push_back({false, 0, label(lab) + (ar ? "(" : "")});
+      for (int k = 0; k < ar; k++) {
+        if (k) next.push_back({false, 0, ", "});
+        next.push_back({true, nd.aux[k], std::string()});
+      }
+      if (ar) next.push_back({false, 0, ")"});
+    }
+    pieces.swap(next);
+  }
+  // render the pending subterms: the depth-first walk of read_net, names
+  // as placeholders
+  std::vector<size_t> todo;
+  for (size_t i = 0; i < pieces.size(); i++)
+    if (pieces[i].sub) todo.push_back(i);
+  HostPool::get().run((int32_t)todo.size(), 1, [&](int32_t lo, int32_t hi) {
+    struct Item { uint32_t w; char emit; };
+    std::vector<Item> st;
+    for (int32_t t = lo; t < hi; t++) {
+      Piece& p = pieces[todo[(size_t)t]];
+      std::string& s = p.text;
+      int64_t got = 0;
+      uint64_t budget = n_nodes + n_vars + 16;
+      st.assign(1, Item{p.w, 0});
+      while (!st.empty()) {
+        const Item it = st.back();
+        st.pop_back();
+        if (it.emit) {
+          s += it.emit == ',' ? ", " : ")";
+          continue;
+        }
+        if (budget-- == 0) {
+          truncated = true;
+          exhausted = true;
+          break;
+        }
+        const uint32_t w = resolve(it.w);
+        if (!is_agent(w)) {
+          name_mark(s, w);
+          continue;
+        }
+        const uint32_t a = idx_of(w);
+        if (a >= n_nodes) {
+          truncated = true;
+          continue;
+        }
+        got++;
+        const int lab = nodes[a].head & 0xFF, ar = arity(lab);
+        s += label(lab);
+        if (ar == 0) continue;
+        s += '(';
+        st.push_back({0, ')'});
+        for (int k = ar - 1; k >= 0; k--) {
+          const uint32_t cw = resolve(nodes[a].aux[k]);
+          if (is_agent(cw) && idx_of(cw) < n_nodes) __builtin_prefetch(nodes + idx_of(cw));
+          st.push_back({cw, 0});
+          if (k) st.push_back({0, ','});
+        }
+      }
+      p.sub = false;
+      reached += got;
+    }
+  });
+  // join, renaming the names in order of first occurrence
+  size_t total = 0;
+  for (const Piece& p : pieces) total += p.text.size();
+  std::string& s = out.text;
+  s.reserve(total);
+  std::unordered_map<uint32_t, int64_t> canon;
+  for (const Piece& p : pieces) {
+    const std::string& t = p.text;
+    size_t i = 0;
+    while (i < t.size()) {
+      const size_t m = t.find(kOpen, i);
+      if (m == std::string::npos) {
+        s.append(t, i, std::string::npos);
+        break;
+      }
+      s.append(t, i, m - i);
+      const uint32_t w = (uint32_t)strtoul(t.substr(m + 1, 8).c_str(), nullptr, 16);
+      auto c = canon.find(w);
+      int64_t k;
+      if (c == canon.end()) {
+        k = (int64_t)canon.size();
+        canon.emplace(w, k);
+      } else {
+        k = c->second;
+      }
+      s += "x" + std::to_string(k);
+      i = m + 10;  // kOpen, 8 hex digits, kClose
+    }
+  }
+  out.reached = reached;
+  out.truncated = truncated;
+  // (a walk that ran out of its budget leaves no numeral, as in read_net)
+  out.nat = exhausted ? -1 : numeral_of(nodes, n_nodes, vars, n_vars, iface, rules);
 }
 
 }  // namespace inet

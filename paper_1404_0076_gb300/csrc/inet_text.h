@@ -54,5 +54,9 @@ struct Readback {
 void read_net(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_t n_vars,
               const std::vector<uint32_t>& iface, const CompiledRules& rules, size_t max_chars,
               bool want_text, Readback& out);
+// The same text as read_net without a character limit, rendered on several
+// host threads (for large normal forms).
+void read_net_text(const Node* nodes, uint64_t n_nodes, const uint32_t* vars, uint64_t n_vars,
+                   const std::vector<uint32_t>& iface, const CompiledRules& rules, Readback& out);
 
 }  // namespace inet
