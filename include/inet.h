@@ -189,9 +189,11 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
 
 /* inet_load_net() for n nets in one call: net i is the text
  * buf[offsets[i] .. offsets[i+1]) (offsets has n + 1 entries).  The texts
- * are parsed on several host threads and staged in order; ids_out[i] gets
- * net i's id.  Stops at the first net that fails (its error is returned) with
- * *n_loaded_out = the number of nets loaded before it. */
+ * are parsed and placed on a process-wide pool of host threads (started on
+ * first use; a call made while another runs, or in a process forked after
+ * the pool started, works on the calling thread) and staged in order;
+ * ids_out[i] gets net i's id.  Stops at the first net that fails (its error
+ * is returned) with *n_loaded_out = the number of nets loaded before it. */
 inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offsets, int32_t n, int32_t* ids_out,
                            int32_t* n_loaded_out);
 
@@ -217,7 +219,10 @@ inet_status inet_transfer_bytes(const inet_ctx* ctx, uint64_t* h2d_out, uint64_t
 /* Writes the net's interface after ->col and ->sub (Sec. 2.2; Theorem 1),
  * terms left to right, names renamed x0, x1, .. in order of first
  * occurrence, as a NUL-terminated string.  If cap is too small returns
- * INET_ERR_INVALID_ARG with *needed_out set (needed_out may be NULL). */
+ * INET_ERR_INVALID_ARG with *needed_out set (needed_out may be NULL).  The
+ * text is rendered from a host snapshot of the arena, on the pool of host
+ * threads, and kept until the arena changes, so a size query followed by
+ * the copy renders it once. */
 inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, size_t* needed_out);
 
 /* If the net's interface is a single numeral S^k(Z), stores k.  Otherwise
