@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "inet_text.h"
@@ -163,6 +164,28 @@ int main() {
     cases++;
     with_names += a.text.find('x') != std::string::npos ? 1 : 0;
     large += a.reached > 10000 ? 1 : 0;
+  }
+  // two renderers at once (the second finds the host pool busy and renders
+  // on its own thread): both must still equal the sequential walk
+  {
+    Arena A1, A2;
+    Gen g1(1001, rules, A1), g2(1002, rules, A2);
+    std::vector<uint32_t> i1{g1.wrap(g1.term(200000, 0))}, i2{g2.wrap(g2.term(200000, 0))};
+    for (uint32_t w : g1.open_names) i1.push_back(w);
+    for (uint32_t w : g2.open_names) i2.push_back(w);
+    Readback s1, s2, p1, p2;
+    read_net(A1.nodes.data(), A1.nodes.size(), A1.vars.data(), A1.vars.size(), i1, rules, (size_t)-1 / 2, true, s1);
+    read_net(A2.nodes.data(), A2.nodes.size(), A2.vars.data(), A2.vars.size(), i2, rules, (size_t)-1 / 2, true, s2);
+    std::thread t([&] {
+      read_net_text(A2.nodes.data(), A2.nodes.size(), A2.vars.data(), A2.vars.size(), i2, rules, p2);
+    });
+    read_net_text(A1.nodes.data(), A1.nodes.size(), A1.vars.data(), A1.vars.size(), i1, rules, p1);
+    t.join();
+    if (s1.text != p1.text || s2.text != p2.text || s1.reached != p1.reached || s2.reached != p2.reached) {
+      std::printf("mismatch with two renderers at once\n");
+      return 1;
+    }
+    cases++;
   }
   std::printf("ok %d cases, %d with free names, %d with more than 10000 agents\n", cases, with_names, large);
   return 0;
