@@ -273,6 +273,23 @@ def test_async_full_size_configs(orc, cfg):
     assert st["interactions"] == sum(x["interactions"] for x in o)
 
 
+_MUL_ORACLE = {}
+
+
+@pytest.mark.parametrize("block,grid", [(64, 1216), (128, 608), (256, 304), (256, 152)])
+def test_async_mul_batch_in_the_bench_shapes(orc, block, grid):
+    # the 2048-net Mul batch in the launch shapes the autotuner picks for the
+    # bench (16 warps per SM) and one block per SM, every net against the oracle
+    nets = full_config(1)
+    if "o" not in _MUL_ORACLE:
+        _MUL_ORACLE["o"] = orc.run(R, nets, quiet=True, threads=os.cpu_count() or 4)
+    o = _MUL_ORACLE["o"]
+    st, g, _ = run_gpu(R, nets, "async", text=False, block=block, grid=grid, max_agents=1 << 24,
+                       max_vars=1 << 24, max_pairs=1 << 20, max_nets=4096)
+    compare(o, g, text=False)
+    assert st["interactions"] == sum(x["interactions"] for x in o) == 47391647
+
+
 def test_async_slices_are_resumable(orc):
     nets = [W.fib_net(17), W.mul_net(12, 11)]
     o = orc.run(R, nets)
