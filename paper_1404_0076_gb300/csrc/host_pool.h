@@ -24,9 +24,12 @@ class HostPool {
  public:
   using Body = std::function<void(int32_t, int32_t)>;
 
+  // Never destroyed: its threads wait for work until the process ends, and
+  // a process forked after they started (which has the objects but not the
+  // threads) must not join or detach them when it exits.
   static HostPool& get() {
-    static HostPool pool;
-    return pool;
+    static HostPool* pool = new HostPool();
+    return *pool;
   }
 
   // body(lo, hi) over [0, n) in ranges of `grain`, on the workers and the
@@ -60,19 +63,6 @@ class HostPool {
     body_ = nullptr;
   }
 
-  ~HostPool() {
-    {
-      std::lock_guard<std::mutex> lk(mu_);
-      quit_ = true;
-    }
-    cv_.notify_all();
-    for (auto& t : workers_)
-      if (t.joinable()) {
-        if (getpid() == pid_) t.join();
-        else t.detach();
-      }
-  }
-
  private:
   HostPool() : pid_(getpid()) {}
 
@@ -96,8 +86,7 @@ class HostPool {
     uint64_t seen = 0;
     for (;;) {
       std::unique_lock<std::mutex> lk(mu_);
-      cv_.wait(lk, [&] { return quit_ || gen_ != seen; });
-      if (quit_) return;
+      cv_.wait(lk, [&] { return gen_ != seen; });
       seen = gen_;
       const Body* b = body_;
       const int32_t n = n_, grain = grain_;
@@ -119,7 +108,6 @@ class HostPool {
   int32_t n_ = 0, grain_ = 1;
   std::atomic<int32_t> next_{0};
   int active_ = 0;
-  bool quit_ = false;
 };
 
 }  // namespace inet

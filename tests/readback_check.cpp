@@ -3,8 +3,12 @@
 // read_net, on random forests of terms laid out at random in an arena
 // (agents reached directly or through chains of bound name slots, free
 // names occurring twice, numerals), small and large.
+#include <sys/wait.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <random>
 #include <string>
 #include <thread>
@@ -183,6 +187,28 @@ int main() {
     t.join();
     if (s1.text != p1.text || s2.text != p2.text || s1.reached != p1.reached || s2.reached != p2.reached) {
       std::printf("mismatch with two renderers at once\n");
+      return 1;
+    }
+    cases++;
+  }
+  // a process forked after the pool started renders on its own thread and
+  // exits normally
+  {
+    Arena A1;
+    Gen g1(2001, rules, A1);
+    std::vector<uint32_t> i1{g1.wrap(g1.term(50000, 0))};
+    for (uint32_t w : g1.open_names) i1.push_back(w);
+    Readback s1;
+    read_net(A1.nodes.data(), A1.nodes.size(), A1.vars.data(), A1.vars.size(), i1, rules, (size_t)-1 / 2, true, s1);
+    const pid_t pid = fork();
+    if (pid == 0) {
+      Readback p1;
+      read_net_text(A1.nodes.data(), A1.nodes.size(), A1.vars.data(), A1.vars.size(), i1, rules, p1);
+      std::exit(p1.text == s1.text ? 0 : 3);
+    }
+    int status = 0;
+    if (pid < 0 || waitpid(pid, &status, 0) != pid || !WIFEXITED(status) || WEXITSTATUS(status) != 0) {
+      std::printf("forked renderer failed\n");
       return 1;
     }
     cases++;

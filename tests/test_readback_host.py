@@ -18,4 +18,4 @@ def test_parallel_text_readback_matches_the_sequential_walk():
                         "-o", exe], check=True)
         p = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert p.returncode == 0, p.stdout + p.stderr
-    assert p.stdout.startswith("ok 61 cases")
+    assert p.stdout.startswith("ok 62 cases")
