@@ -253,16 +253,17 @@ def serving_leg(args, local: int) -> dict:
     srv = Server(W.ARITH_RULES, device=local, budget_bytes=budget, epoch_us=args.serve_epoch_us, max_pairs=1 << 23)
     out = {"workload": "serving mix: Poisson arrivals, one net each from add/mul/ack/fib, sizes lognormal "
                        "(median 1e3 interactions, sigma 2.16, clipped to 1e7), seed 14040076+4",
-           "requests": len(reqs), "mean_request_interactions": mean_size, "budget_bytes": budget, "arenas": 2,
+           "requests": len(reqs), "mean_request_interactions": mean_size, "budget_bytes": budget, "arenas": 1,
            "epoch_us": args.serve_epoch_us, "sample": f"first {len(reqs)} of the 100000-request stream"}
 
     def run(scale: float) -> dict:
-        e0, s0 = srv.epochs, srv.switches
+        e0, s0, n0 = srv.epochs, srv.frees, srv.freed
         t0 = time.perf_counter()
         done = srv.serve(reqs, time_scale=scale)
         wall = time.perf_counter() - t0
         rec = summarize(done, wall)
-        rec.update(wall_s=wall, epochs=srv.epochs - e0, arena_switches=srv.switches - s0,
+        rec.update(wall_s=wall, epochs=srv.epochs - e0, free_calls=srv.frees - s0, nets_freed=srv.freed - n0,
+                   arena_switches=0,
                    wrong=sum(1 for d in done if d.status != "OK"
                              or (d.value, d.interactions) != (expect[d.rid], reqs[d.rid].size)))
         return rec

@@ -276,6 +276,38 @@ inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int3
 inet_status inet_readback_nats_end(inet_ctx* ctx, int32_t wait, uint64_t* values_out, uint64_t* interactions_out,
                                    int32_t cap, int32_t* n_out);
 
+/* Returns every slot the listed nets still hold to the free rings: their
+ * agents (found by the net id in each agent record) and their name slots
+ * (found by the owner array), so that later loads and reductions reuse the
+ * memory; the ids themselves are released too and handed out again by
+ * later loads.  Nets are independent configurations (Sec. 2.2,
+ * Configurations): nothing outside a net can reach its agents or names, so
+ * once its result has been read back (->col / ->sub, Theorem 1) it can go.
+ * Every listed net must have been staged or reduced and must have no active
+ * pair left (normal form, or stopped by INET_ERR_NO_RULE); otherwise
+ * INET_ERR_STATE and nothing is freed.  A net listed twice is
+ * INET_ERR_INVALID_ARG; a net in the non-blocking readback in flight is
+ * INET_ERR_STATE.  At most 65536 nets per call.  One scan over every agent
+ * and name slot in use (about 20 bytes of device traffic per slot), so a
+ * request loop frees finished nets in batches.  After the call the ids are
+ * unknown (INET_ERR_INVALID_ARG) until a load reuses them.  Loads place new
+ * nets into freed slots before using never-used ones (inet_stage /
+ * inet_reduce upload them above the bump pointers and move the top part
+ * into slots the rings hold). */
+inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n);
+
+/* inet_free_nets() for one net. */
+inet_status inet_free_net(inet_ctx* ctx, int32_t net_id);
+
+/* How much of the arena is in use: *agent_slots_out and *name_slots_out get
+ * the bump pointers (slots handed out at least once since the last reset;
+ * each slot below them is live or waits in a free ring), *live_agents_out the
+ * agents alive in all nets.  Loaded nets are uploaded and placed first, so
+ * the figures include them.  Any pointer may be NULL.  The paper has no
+ * counterpart: it lets a request loop see that freed memory is reused. */
+inet_status inet_arena_usage(inet_ctx* ctx, uint64_t* agent_slots_out, uint64_t* name_slots_out,
+                             int64_t* live_agents_out);
+
 /* Per-net counters; live and residual agents come from the readback
  * snapshot. */
 inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out);

@@ -147,6 +147,14 @@ class Evaluator:
             self._rb_bufs = capi_lazy.readback_buffers()
         return capi_lazy.inet_readback_nats_end(self.ctx, wait, self._rb_bufs)
 
+    def free(self, net_ids) -> None:
+        """Returns the slots and ids of finished nets for reuse (inet_free_nets)."""
+        capi_lazy.inet_free_nets(self.ctx, list(net_ids))
+
+    def arena_usage(self) -> dict:
+        """Bump pointers (agent and name slots handed out) and live agents."""
+        return capi_lazy.inet_arena_usage(self.ctx)
+
     def net_info(self, net_id: int) -> dict:
         return capi_lazy.inet_net_info(self.ctx, net_id)
 

@@ -45,6 +45,7 @@ EXPORTED = [
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
     "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
+    "inet_free_nets", "inet_free_net", "inet_arena_usage",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -102,6 +103,9 @@ def _load():
         "inet_reduce": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(inet_reduce_opts),
                          C.POINTER(inet_reduce_stats)], C.c_int32),
         "inet_stage": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
+        "inet_free_nets": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
+        "inet_free_net": ([P, C.c_int32], C.c_int32),
+        "inet_arena_usage": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_int64)], C.c_int32),
         "inet_transfer_bytes": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
         "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
@@ -222,6 +226,21 @@ def inet_reduce(ctx, net_ids, opts: inet_reduce_opts | None = None, check: bool 
 def inet_stage(ctx, net_ids) -> None:
     ids = (C.c_int32 * len(net_ids))(*net_ids)
     _check(ctx, LIB.inet_stage(ctx, ids, len(net_ids)))
+
+
+def inet_free_nets(ctx, net_ids) -> None:
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    _check(ctx, LIB.inet_free_nets(ctx, ids, len(net_ids)))
+
+
+def inet_free_net(ctx, net_id: int) -> None:
+    _check(ctx, LIB.inet_free_net(ctx, net_id))
+
+
+def inet_arena_usage(ctx) -> dict:
+    a, v, live = C.c_uint64(), C.c_uint64(), C.c_int64()
+    _check(ctx, LIB.inet_arena_usage(ctx, C.byref(a), C.byref(v), C.byref(live)))
+    return {"agent_slots": a.value, "name_slots": v.value, "live_agents": live.value}
 
 
 def inet_transfer_bytes(ctx) -> tuple[int, int]:

@@ -17,6 +17,7 @@
 #include "inet_kernels.cuh"
 #include "inet_micro.cuh"
 #include "inet_control.cuh"
+#include "inet_free.cuh"
 #include "inet_paper.cuh"
 #include "inet_readback.cuh"
 #include "inet_text.h"
@@ -39,8 +40,9 @@ constexpr uint32_t kMaxSolo = 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Layout {
-  size_t ctrl, node, var, front0, front1, qseq, afree, vfree, netctr, netstat, netrep, hist, table, tmpl, arity,
-      trace_front, trace_live, rb_root, rb_val, fin_ids, fin_cnt, total;
+  size_t ctrl, node, var, vown, front0, front1, qseq, afree, vfree, netctr, netstat, netrep, netmark, hist, table,
+      tmpl, arity, trace_front, trace_live, rb_root, rb_val, fin_ids, fin_cnt, free_ids, free_st, stn_ids, stn_ctr,
+      total;
 };
 
 inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
@@ -66,6 +68,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.ctrl = take(sizeof(Ctrl));
   L.node = take(sizeof(Node) * c.max_agents);
   L.var = take(sizeof(uint32_t) * c.max_vars);
+  L.vown = take(sizeof(uint32_t) * c.max_vars);
   L.front0 = take(sizeof(Pair) * c.max_pairs);
   L.front1 = take(sizeof(Pair) * c.max_pairs);
   L.qseq = take(sizeof(unsigned long long) * c.max_pairs);
@@ -74,6 +77,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.netctr = take(sizeof(unsigned long long) * c.max_nets);
   L.netstat = take(sizeof(int32_t) * c.max_nets);
   L.netrep = take(sizeof(uint32_t) * c.max_nets);
+  L.netmark = take(c.max_nets);
   L.hist = take(sizeof(unsigned long long) * INET_MAX_RULES);
   L.table = take(sizeof(int16_t) * kMaxLabels * kMaxLabels);
   L.tmpl = take(sizeof(Template) * INET_MAX_RULES);
@@ -84,12 +88,17 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.rb_val = take(sizeof(unsigned long long) * kReadChunk);
   L.fin_ids = take(sizeof(int32_t) * kReadChunk);
   L.fin_cnt = take(sizeof(uint32_t));
+  L.free_ids = take(sizeof(int32_t) * kReadChunk);
+  L.free_st = take(sizeof(unsigned long long) * 4);
+  L.stn_ids = take(sizeof(int32_t) * kReadChunk);
+  L.stn_ctr = take(sizeof(unsigned long long) * kReadChunk);
   L.total = take(0) + 256;
   return L;
 }
 
 struct NetRec {
   bool used = false;
+  bool uploaded = false;          // its records and counter are on the device
   bool started = false;           // its pairs were handed to the device
   std::vector<uint32_t> iface;
   std::vector<Pair> pairs;        // initial active pairs, until started
@@ -125,8 +134,10 @@ struct inet_ctx {
   uint64_t st_a0 = 0;
   std::vector<uint32_t> st_vars;
   uint64_t st_v0 = 0;
+  std::vector<uint32_t> st_vown;            // owning net of each staged name slot
   std::vector<unsigned long long> st_netctr;
-  uint32_t st_net0 = 0;
+  std::vector<int32_t> st_net_ids;          // ids of the staged nets, parallel to st_netctr
+  std::vector<int32_t> free_net_ids;        // ids released by inet_free_nets, reused by loads
   // device-side per-net copies (after the last reduce)
   std::vector<unsigned long long> h_netctr;
   std::vector<int32_t> h_netstat;
@@ -157,6 +168,7 @@ struct inet_ctx {
   uint32_t* rb_host_roots = nullptr;       // pinned, kReadChunk entries
   unsigned long long* rb_host_vals = nullptr;
   std::vector<uint64_t> rb_inter;           // interactions of the batch in flight
+  std::vector<int32_t> rb_ids;              // its nets
   int32_t rb_n = -1;                        // nets of the batch in flight, -1: none
   // list-ranking scratch of the numeral readback: two buffers of
   // (successor, weight) per agent and name slot, and its control words
@@ -219,6 +231,7 @@ void fill_dev(inet_ctx* ctx) {
   d.qseq = at<unsigned long long>(ctx, L.qseq);
   d.afree = at<uint32_t>(ctx, L.afree);
   d.vfree = at<uint32_t>(ctx, L.vfree);
+  d.vown = at<uint32_t>(ctx, L.vown);
   d.netctr = at<unsigned long long>(ctx, L.netctr);
   d.netstat = at<int32_t>(ctx, L.netstat);
   d.netrep = at<uint32_t>(ctx, L.netrep);
@@ -272,6 +285,7 @@ inet_status clear_device(inet_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netctr, 0, sizeof(unsigned long long) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netstat, 0, sizeof(int32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netrep, 0, sizeof(uint32_t) * ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.netmark, 0, ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
   uint32_t never = 0xFFFFFFFFu;
   CK(h2d(ctx, &ctx->dev.ctrl->stop_step, &never, 4));
@@ -295,36 +309,113 @@ inet_status ensure_workspace(inet_ctx* ctx) {
   return upload_rules(ctx);
 }
 
-// Copies staged nets to the device and the host-side counters to the control block.
+// Copies staged nets to the device and the host-side counters to the
+// control block, then places them: the uploaded range sits above the bump
+// pointers, and its top part moves into slots the free rings hold (slots of
+// consumed agents, finished names and freed nets), so that a context that
+// frees nets reuses their memory (inet_free.cuh).  The host learns which
+// slots were taken and rewrites the words it keeps: interfaces, and the
+// initial pairs of nets not handed to the device yet.
 inet_status upload_staged(inet_ctx* ctx) {
-  if (!ctx->st_nodes.empty())
-    CK(h2d(ctx, ctx->dev.node + ctx->st_a0, ctx->st_nodes.data(), ctx->st_nodes.size() * sizeof(Node)));
-  if (!ctx->st_vars.empty())
-    CK(h2d(ctx, ctx->dev.var + ctx->st_v0, ctx->st_vars.data(), ctx->st_vars.size() * sizeof(uint32_t)));
-  if (!ctx->st_netctr.empty()) {
-    CK(h2d(ctx, ctx->dev.netctr + ctx->st_net0, ctx->st_netctr.data(),
-                       ctx->st_netctr.size() * sizeof(unsigned long long)));
-    CK(cudaMemsetAsync(ctx->dev.netstat + ctx->st_net0, 0, ctx->st_netctr.size() * sizeof(int32_t), ctx->stream));
-  }
   const bool any = !ctx->st_nodes.empty() || !ctx->st_vars.empty() || !ctx->st_netctr.empty();
-  if (any) {
-    static thread_local unsigned long long hb[2];
-    static thread_local long long hl;
-    hb[0] = ctx->a_bump;
-    hb[1] = ctx->v_bump;
-    hl = ctx->live;
-    CK(h2d(ctx, &ctx->dev.ctrl->a_bump, &hb[0], 8));
-    CK(h2d(ctx, &ctx->dev.ctrl->v_bump, &hb[1], 8));
-    CK(h2d(ctx, &ctx->dev.ctrl->live, &hl, 8));
-    CK(cudaStreamSynchronize(ctx->stream));
+  if (!any) {
+    ctx->st_a0 = ctx->a_bump;
+    ctx->st_v0 = ctx->v_bump;
+    return INET_OK;
   }
+  const uint64_t a0 = ctx->st_a0, v0 = ctx->st_v0;
+  const uint32_t ta = (uint32_t)ctx->st_nodes.size(), tv = (uint32_t)ctx->st_vars.size();
+  if (a0 + ta != ctx->a_bump || v0 + tv != ctx->v_bump)
+    return fail(ctx, INET_ERR_STATE, "staged nets do not end at the bump pointers");
+  if (ta) CK(h2d(ctx, ctx->dev.node + a0, ctx->st_nodes.data(), (size_t)ta * sizeof(Node)));
+  if (tv) {
+    CK(h2d(ctx, ctx->dev.var + v0, ctx->st_vars.data(), (size_t)tv * sizeof(uint32_t)));
+    CK(h2d(ctx, ctx->dev.vown + v0, ctx->st_vown.data(), (size_t)tv * sizeof(uint32_t)));
+  }
+  const size_t nn = ctx->st_netctr.size();
+  if (nn) {
+    bool run = true;  // ids id0, id0 + 1, ..: one copy and two clears
+    for (size_t i = 1; i < nn && run; i++) run = ctx->st_net_ids[i] == ctx->st_net_ids[0] + (int32_t)i;
+    if (run) {
+      const int32_t id0 = ctx->st_net_ids[0];
+      CK(h2d(ctx, ctx->dev.netctr + id0, ctx->st_netctr.data(), nn * sizeof(unsigned long long)));
+      CK(cudaMemsetAsync(ctx->dev.netstat + id0, 0, nn * sizeof(int32_t), ctx->stream));
+      CK(cudaMemsetAsync(ctx->dev.netrep + id0, 0, nn * sizeof(uint32_t), ctx->stream));
+    } else {
+      int32_t* dids = at<int32_t>(ctx, ctx->lay.stn_ids);
+      unsigned long long* dctr = at<unsigned long long>(ctx, ctx->lay.stn_ctr);
+      for (size_t off = 0; off < nn; off += kReadChunk) {
+        const uint32_t m = (uint32_t)std::min<size_t>(nn - off, kReadChunk);
+        CK(h2d(ctx, dids, ctx->st_net_ids.data() + off, m * sizeof(int32_t)));
+        CK(h2d(ctx, dctr, ctx->st_netctr.data() + off, m * sizeof(unsigned long long)));
+        k_net_ctr_scatter<<<(m + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, dids, dctr, m);
+        CK(cudaGetLastError());
+        if (off + m < nn) CK(cudaStreamSynchronize(ctx->stream));  // the id buffers are reused
+      }
+    }
+  }
+  static thread_local unsigned long long hb[2];
+  static thread_local long long hl;
+  static thread_local unsigned long long pl[4];
+  hb[0] = ctx->a_bump;
+  hb[1] = ctx->v_bump;
+  hl = ctx->live;
+  pl[0] = pl[1] = pl[2] = pl[3] = 0;
+  CK(h2d(ctx, &ctx->dev.ctrl->a_bump, &hb[0], 8));
+  CK(h2d(ctx, &ctx->dev.ctrl->v_bump, &hb[1], 8));
+  CK(h2d(ctx, &ctx->dev.ctrl->live, &hl, 8));
+  if (ta || tv) {
+    const unsigned grid = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((std::max(ta, tv) + 255) / 256, 8ull * (uint64_t)std::max(ctx->num_sms, 1)));
+    k_place_prep<<<1, 1, 0, ctx->stream>>>(ctx->dev, ta, tv);
+    k_place<<<grid, 256, 0, ctx->stream>>>(ctx->dev, (uint32_t)a0, ta, (uint32_t)v0, tv);
+    k_place_post<<<1, 1, 0, ctx->stream>>>(ctx->dev, (uint32_t)a0, ta, (uint32_t)v0, tv);
+    CK(cudaGetLastError());
+    CK(d2h(ctx, pl, &ctx->dev.ctrl->place_ka, sizeof pl));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  const uint32_t ka = (uint32_t)pl[0], kv = (uint32_t)pl[1];
+  if (ka > ta || kv > tv) return fail(ctx, INET_ERR_STATE, "placement took more slots than were uploaded");
+  if (ka || kv) {
+    // the slots taken, in ring order
+    std::vector<uint32_t> as(ka), vs(kv);
+    auto seg = [&](std::vector<uint32_t>& out, const uint32_t* ring, uint64_t cap, uint64_t h) -> cudaError_t {
+      const uint64_t k = out.size(), first = std::min<uint64_t>(k, cap - h);
+      cudaError_t e = cudaSuccess;
+      if (first) e = d2h(ctx, out.data(), ring + h, first * 4);
+      if (e == cudaSuccess && k > first) e = d2h(ctx, out.data() + first, ring, (k - first) * 4);
+      return e;
+    };
+    CK(seg(as, ctx->dev.afree, ctx->cfg.max_agents, pl[2]));
+    CK(seg(vs, ctx->dev.vfree, ctx->cfg.max_vars, pl[3]));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const uint64_t amov = a0 + ta - ka, vmov = v0 + tv - kv;
+    auto ta_of = [&](uint32_t i) -> uint32_t { return i >= amov && i < a0 + ta ? as[i - amov] : i; };
+    auto tr = [&](uint32_t w) -> uint32_t {
+      if (is_agent(w)) return mk_agent(ta_of(idx_of(w)));
+      if (is_var(w) && idx_of(w) >= vmov && idx_of(w) < v0 + tv) return mk_var(vs[idx_of(w) - vmov]);
+      return w;
+    };
+    for (int32_t id : ctx->st_net_ids) {
+      NetRec& nr = ctx->nets[(size_t)id];
+      for (uint32_t& w : nr.iface) w = tr(w);
+      for (Pair& p : nr.pairs) {
+        p.a = ta_of(p.a);
+        p.b = ta_of(p.b);
+      }
+    }
+  }
+  ctx->a_bump = a0 + ta - ka;
+  ctx->v_bump = v0 + tv - kv;
+  for (int32_t id : ctx->st_net_ids) ctx->nets[(size_t)id].uploaded = true;
   ctx->st_nodes.clear();
   ctx->st_vars.clear();
+  ctx->st_vown.clear();
   ctx->st_netctr.clear();
+  ctx->st_net_ids.clear();
   ctx->st_a0 = ctx->a_bump;
   ctx->st_v0 = ctx->v_bump;
-  ctx->st_net0 = (uint32_t)ctx->nets.size();
-  if (any) ctx->snap_valid = false;
+  ctx->snap_valid = false;
   return INET_OK;
 }
 
@@ -332,11 +423,15 @@ inet_status upload_staged(inet_ctx* ctx) {
 // reduction changed them (nets not uploaded yet keep their host values).
 inet_status ensure_net_counters(inet_ctx* ctx) {
   if (ctx->h_net_valid || ctx->host_only || !ctx->ws_ready) return INET_OK;
-  const size_t up = std::min<size_t>(ctx->st_net0, ctx->nets.size());
-  if (up) {
-    CK(d2h(ctx, ctx->h_netctr.data(), ctx->dev.netctr, up * sizeof(unsigned long long)));
-    CK(d2h(ctx, ctx->h_netstat.data(), ctx->dev.netstat, up * sizeof(int32_t)));
+  const size_t nn = ctx->nets.size();
+  if (nn) {
+    CK(d2h(ctx, ctx->h_netctr.data(), ctx->dev.netctr, nn * sizeof(unsigned long long)));
+    CK(d2h(ctx, ctx->h_netstat.data(), ctx->dev.netstat, nn * sizeof(int32_t)));
     CK(cudaStreamSynchronize(ctx->stream));
+  }
+  for (size_t i = 0; i < ctx->st_net_ids.size(); i++) {
+    ctx->h_netctr[(size_t)ctx->st_net_ids[i]] = ctx->st_netctr[i];
+    ctx->h_netstat[(size_t)ctx->st_net_ids[i]] = 0;
   }
   ctx->h_net_valid = true;
   return INET_OK;
@@ -520,6 +615,32 @@ inet_status stage_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
   return INET_OK;
 }
 
+// The id the k-th net of a load would get (k = 0, 1, ..): ids released by
+// inet_free_nets first (most recent first), then never-used ones.  Nothing
+// is committed; -1 when the context is out of net slots.
+int32_t peek_net_id(const inet_ctx* ctx, size_t k) {
+  const size_t nf = ctx->free_net_ids.size();
+  if (k < nf) return ctx->free_net_ids[nf - 1 - k];
+  const size_t fresh = ctx->nets.size() + (k - nf);
+  return fresh < ctx->cfg.max_nets ? (int32_t)fresh : -1;
+}
+
+// Commits net `id` (the next id peek_net_id gave) with its record.
+void commit_net(inet_ctx* ctx, int32_t id, NetRec&& nr, unsigned long long ctr) {
+  if (!ctx->free_net_ids.empty() && ctx->free_net_ids.back() == id) {
+    ctx->free_net_ids.pop_back();
+    ctx->nets[(size_t)id] = std::move(nr);
+    ctx->h_netctr[(size_t)id] = ctr;
+    ctx->h_netstat[(size_t)id] = 0;
+  } else {
+    ctx->nets.push_back(std::move(nr));
+    ctx->h_netctr.push_back(ctr);
+    ctx->h_netstat.push_back(0);
+  }
+  ctx->st_netctr.push_back(ctr);
+  ctx->st_net_ids.push_back(id);
+}
+
 // Device buffers of one control run, freed on every exit.
 struct CtlBufs {
   std::vector<void*> p;
@@ -667,13 +788,14 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
   if (!ctx || (!text && len) || !net_id_out) return INET_ERR_INVALID_ARG;
   if (!ctx->have_rules) return fail(ctx, INET_ERR_STATE, "load rules first");
   if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
-  if (ctx->nets.size() >= ctx->cfg.max_nets) return fail(ctx, INET_ERR_ARENA_FULL, "no free net slot");
+  const int32_t id = peek_net_id(ctx, 0);
+  if (id < 0) return fail(ctx, INET_ERR_ARENA_FULL, "no free net slot");
   if (!ctx->host_only) {
     DeviceGuard g(ctx->device);
     inet_status s = ensure_workspace(ctx);
     if (s) return s;
   }
-  const uint32_t slot = (uint32_t)ctx->nets.size();
+  const uint32_t slot = (uint32_t)id;
   FlatNet fn;
   std::string err;
   int rc = flatten_net(std::string(text ? text : "", len), ctx->rules, slot, (uint32_t)ctx->a_bump,
@@ -684,23 +806,21 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
   if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
     ctx->st_a0 = ctx->a_bump;
     ctx->st_v0 = ctx->v_bump;
-    ctx->st_net0 = slot;
   }
   ctx->st_nodes.insert(ctx->st_nodes.end(), fn.nodes.begin(), fn.nodes.end());
   ctx->st_vars.insert(ctx->st_vars.end(), fn.vars.begin(), fn.vars.end());
-  ctx->st_netctr.push_back((unsigned long long)fn.pairs.size() << kNetPairShift);
+  ctx->st_vown.insert(ctx->st_vown.end(), fn.vars.size(), slot);
   ctx->a_bump += fn.nodes.size();
   ctx->v_bump += fn.vars.size();
   ctx->live += (int64_t)fn.nodes.size();
   NetRec nr;
   nr.used = true;
   nr.iface = std::move(fn.iface);
+  const unsigned long long ctr = (unsigned long long)fn.pairs.size() << kNetPairShift;
   nr.pairs = std::move(fn.pairs);
-  ctx->nets.push_back(std::move(nr));
-  ctx->h_netctr.push_back((unsigned long long)ctx->nets.back().pairs.size() << kNetPairShift);
-  ctx->h_netstat.push_back(0);
+  commit_net(ctx, id, std::move(nr), ctr);
   ctx->snap_valid = false;
-  *net_id_out = (int32_t)slot;
+  *net_id_out = id;
   return INET_OK;
 }
 
@@ -722,7 +842,9 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
   // net that does not fit ends the batch, the nets before it stay loaded);
   // then the same threads shift each net's indices to its place and copy it
   // into the staging vectors
-  const uint32_t slot0 = (uint32_t)ctx->nets.size();
+  // ids: released ones first, then never-used ones (-1: out of net slots)
+  std::vector<int32_t> pid((size_t)n);
+  for (int32_t i = 0; i < n; i++) pid[(size_t)i] = peek_net_id(ctx, (size_t)i);
   std::vector<FlatNet> fns((size_t)n);
   std::vector<int> rcs((size_t)n, 0);
   std::vector<std::string> errs((size_t)n);
@@ -730,8 +852,9 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
   auto on_threads = [](int32_t cnt, const HostPool::Body& body) { HostPool::get().run(cnt, 16, body); };
   on_threads(n, [&](int32_t lo, int32_t hi) {
     for (int32_t i = lo; i < hi; i++)
-      rcs[(size_t)i] = flatten_net(std::string(buf + offsets[i], offsets[i + 1] - offsets[i]), ctx->rules,
-                                   slot0 + (uint32_t)i, 0, 0, fns[(size_t)i], errs[(size_t)i]);
+      if (pid[(size_t)i] >= 0)
+        rcs[(size_t)i] = flatten_net(std::string(buf + offsets[i], offsets[i + 1] - offsets[i]), ctx->rules,
+                                     (uint32_t)pid[(size_t)i], 0, 0, fns[(size_t)i], errs[(size_t)i]);
   });
   std::vector<uint64_t> a_at((size_t)n + 1), v_at((size_t)n + 1);
   a_at[0] = ctx->a_bump;
@@ -746,7 +869,7 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
       stop_msg = errs[(size_t)m];
       break;
     }
-    if (ctx->nets.size() + (size_t)m >= ctx->cfg.max_nets) {
+    if (pid[(size_t)m] < 0) {
       stop = INET_ERR_ARENA_FULL;
       stop_msg = "no free net slot";
       break;
@@ -763,15 +886,16 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
     if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
       ctx->st_a0 = ctx->a_bump;
       ctx->st_v0 = ctx->v_bump;
-      ctx->st_net0 = (uint32_t)ctx->nets.size();
     }
     // staged entries continue the staging vectors: slot a_at[i] is entry
     // a_at[i] - st_a0 (likewise for names)
     const size_t na0 = ctx->st_nodes.size(), nv0 = ctx->st_vars.size();
     ctx->st_nodes.resize(na0 + (size_t)(a_at[(size_t)m] - a_at[0]));
     ctx->st_vars.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
+    ctx->st_vown.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
     Node* dn = ctx->st_nodes.data() + na0;
     uint32_t* dv = ctx->st_vars.data() + nv0;
+    uint32_t* downer = ctx->st_vown.data() + nv0;
     on_threads(m, [&](int32_t lo, int32_t hi) {
       for (int32_t i = lo; i < hi; i++) {
         FlatNet& fn = fns[(size_t)i];
@@ -787,6 +911,7 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
         }
         uint32_t* ov = dv + (v_at[(size_t)i] - v_at[0]);
         for (uint32_t w : fn.vars) *ov++ = shift(w);
+        std::fill_n(downer + (v_at[(size_t)i] - v_at[0]), fn.vars.size(), (uint32_t)pid[(size_t)i]);
         for (uint32_t& w : fn.iface) w = shift(w);
         for (Pair& p : fn.pairs) {
           p.a += ab;
@@ -798,19 +923,17 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
     ctx->v_bump = v_at[(size_t)m];
     ctx->live += (int64_t)(a_at[(size_t)m] - a_at[0]);
     ctx->st_netctr.reserve(ctx->st_netctr.size() + (size_t)m);
+    ctx->st_net_ids.reserve(ctx->st_net_ids.size() + (size_t)m);
     ctx->nets.reserve(ctx->nets.size() + (size_t)m);
     for (int32_t i = 0; i < m; i++) {
       FlatNet& fn = fns[(size_t)i];
       const unsigned long long ctr = (unsigned long long)fn.pairs.size() << kNetPairShift;
-      ctx->st_netctr.push_back(ctr);
       NetRec nr;
       nr.used = true;
       nr.iface = std::move(fn.iface);
       nr.pairs = std::move(fn.pairs);
-      ctx->nets.push_back(std::move(nr));
-      ctx->h_netctr.push_back(ctr);
-      ctx->h_netstat.push_back(0);
-      ids_out[i] = (int32_t)(ctx->nets.size() - 1);
+      commit_net(ctx, pid[(size_t)i], std::move(nr), ctr);
+      ids_out[i] = pid[(size_t)i];
     }
     ctx->snap_valid = false;
     *n_loaded_out = m;
@@ -1261,6 +1384,7 @@ inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int3
     CK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->rb_host_vals), sizeof(unsigned long long) * kReadChunk, 0));
   }
   ctx->rb_inter.assign((size_t)n, 0);
+  ctx->rb_ids.assign(net_ids, net_ids + n);
   for (int32_t i = 0; i < n; i++) {
     if ((s = check_net(ctx, net_ids[i]))) return s;
     const NetRec& nr = ctx->nets[(size_t)net_ids[i]];
@@ -1314,6 +1438,7 @@ inet_status inet_readback_nats_end(inet_ctx* ctx, int32_t wait, uint64_t* values
   }
   *n_out = ctx->rb_n;
   ctx->rb_n = -1;
+  ctx->rb_ids.clear();
   return INET_OK;
 }
 
@@ -1325,7 +1450,7 @@ inet_status inet_net_finished(inet_ctx* ctx, int32_t* ids_out, int32_t cap, int3
   inet_status s = ensure_workspace(ctx);
   if (s) return s;
   if ((s = upload_staged(ctx))) return s;
-  const uint32_t nn = (uint32_t)std::min<size_t>(ctx->st_net0, ctx->nets.size());
+  const uint32_t nn = (uint32_t)ctx->nets.size();
   if (nn == 0 || cap == 0) return INET_OK;
   const uint32_t c = (uint32_t)std::min<int32_t>(cap, (int32_t)kReadChunk);
   int32_t* dids = at<int32_t>(ctx, ctx->lay.fin_ids);
@@ -1342,6 +1467,72 @@ inet_status inet_net_finished(inet_ctx* ctx, int32_t* ids_out, int32_t cap, int3
     CK(cudaStreamSynchronize(ctx->stream));
   }
   *n_out = (int32_t)k;
+  return INET_OK;
+}
+
+inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
+  if (!ctx || n < 0 || (uint32_t)n > kReadChunk || (n > 0 && !net_ids)) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  if (n == 0) return INET_OK;
+  std::vector<uint8_t> listed(ctx->nets.size(), 0);
+  for (int32_t i = 0; i < n; i++) {
+    inet_status s = check_net(ctx, net_ids[i]);
+    if (s) return s;
+    if (listed[(size_t)net_ids[i]]) return fail(ctx, INET_ERR_INVALID_ARG, "net listed twice");
+    listed[(size_t)net_ids[i]] = 1;
+    if (!ctx->nets[(size_t)net_ids[i]].started)
+      return fail(ctx, INET_ERR_STATE, "net " + std::to_string(net_ids[i]) + " was never staged or reduced");
+  }
+  if (ctx->rb_n >= 0)
+    for (int32_t id : ctx->rb_ids)
+      if (listed[(size_t)id]) return fail(ctx, INET_ERR_STATE, "a readback of this net is in flight");
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  // every record below the host's bump pointer must be on the device
+  if ((s = upload_staged(ctx))) return s;
+  int32_t* dids = at<int32_t>(ctx, ctx->lay.free_ids);
+  unsigned long long* dst = at<unsigned long long>(ctx, ctx->lay.free_st);
+  uint8_t* mark = at<uint8_t>(ctx, ctx->lay.netmark);
+  CK(h2d(ctx, dids, net_ids, sizeof(int32_t) * (size_t)n));
+  k_free_check<<<1, 1024, 0, ctx->stream>>>(ctx->dev, dids, (uint32_t)n, mark, dst);
+  const uint64_t span = std::max(ctx->a_bump, ctx->v_bump);
+  const unsigned grid = (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>((span + 255) / 256, 8ull * (uint64_t)std::max(ctx->num_sms, 1)));
+  k_free_scan<<<grid, 256, 0, ctx->stream>>>(ctx->dev, (uint32_t)ctx->a_bump, (uint32_t)ctx->v_bump, mark, dst);
+  k_free_unmark<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, dids, (uint32_t)n, mark, dst);
+  CK(cudaGetLastError());
+  static thread_local unsigned long long hs[3];
+  CK(d2h(ctx, hs, dst, sizeof hs));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hs[0]) return fail(ctx, INET_ERR_STATE, "a listed net still has active pairs; nothing was freed");
+  for (int32_t i = 0; i < n; i++) {
+    const size_t id = (size_t)net_ids[i];
+    ctx->nets[id] = NetRec();
+    ctx->h_netctr[id] = 0;
+    ctx->h_netstat[id] = 0;
+    ctx->free_net_ids.push_back(net_ids[i]);
+  }
+  ctx->live -= (int64_t)hs[1];
+  ctx->snap_valid = false;
+  ctx->text_net = -1;
+  return INET_OK;
+}
+
+inet_status inet_free_net(inet_ctx* ctx, int32_t net_id) { return inet_free_nets(ctx, &net_id, 1); }
+
+inet_status inet_arena_usage(inet_ctx* ctx, uint64_t* agent_slots_out, uint64_t* name_slots_out,
+                             int64_t* live_agents_out) {
+  if (!ctx) return INET_ERR_INVALID_ARG;
+  if (!ctx->host_only && ctx->ws_ready) {
+    DeviceGuard g(ctx->device);
+    inet_status s = upload_staged(ctx);
+    if (s) return s;
+  }
+  if (agent_slots_out) *agent_slots_out = ctx->a_bump;
+  if (name_slots_out) *name_slots_out = ctx->v_bump;
+  if (live_agents_out) *live_agents_out = ctx->live;
   return INET_OK;
 }
 
@@ -1401,9 +1592,12 @@ inet_status inet_reset(inet_ctx* ctx) {
   ctx->st_nodes.clear();
   ctx->st_vars.clear();
   ctx->st_netctr.clear();
+  ctx->st_vown.clear();
+  ctx->st_net_ids.clear();
+  ctx->free_net_ids.clear();
+  ctx->rb_ids.clear();
   ctx->a_bump = ctx->v_bump = 0;
   ctx->st_a0 = ctx->st_v0 = 0;
-  ctx->st_net0 = 0;
   ctx->live = 0;
   ctx->step = 0;
   ctx->fcount[0] = ctx->fcount[1] = 0;

@@ -96,6 +96,7 @@ __device__ __forceinline__ bool link_async(const Dev& d, WarpMem& W, uint32_t t,
     const uint32_t old = atomicExch(d.var + x, u);
     if (old == kEmpty) return false;
     __stcg(d.var + x, kEmpty);
+    if (d.vown) __stcg(d.vown + x, kNoNet);
     const int pos = atomicAdd(&W.vstage_n, 1);
     if (pos < kVStageW) {
       W.vstage[pos] = x;
@@ -243,8 +244,12 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
     for (uint32_t v = 0; v < n_fresh; v++) {
       const uint32_t k = ov + v;
       const uint32_t x = k < tv ? W.vstk[vbase + k] : pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, k - tv);
-      if (x >= d.cap_vars) in_range = false;
-      else __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's fence
+      if (x >= d.cap_vars) {
+        in_range = false;
+      } else {
+        __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's fence
+        if (d.vown) __stcg(d.vown + x, net);
+      }
       W.vals[kValFresh + v][lane] = mk_var(x);
     }
     if (!in_range) {
@@ -270,6 +275,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
       for (uint32_t f = 0; f < free_a; f++) {
         const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
         const uint32_t k = of + f;
+        __stcg(&d.node[slot].head, kFreeHead);
         if (k < keep) W.astk[atop + k] = slot;
         else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
       }
@@ -332,6 +338,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
           // second arrival: the slot is finished; continue with old = u
           const uint32_t x = idx_of(t);
           __stcg(d.var + x, kEmpty);
+          if (d.vown) __stcg(d.vown + x, kNoNet);
           const int pos = atomicAdd(&W.vstage_n, 1);
           if (pos < kVStageW) {
             W.vstage[pos] = x;

@@ -63,6 +63,9 @@ struct Ctrl {
   alignas(128) uint32_t aexit;              // pairs written back to the other frontier buffer
   uint32_t qinit;                           // queue sequence numbers initialised since the reset
   unsigned long long qdirty;                // cells [0, qdirty) may hold a previous launch's sequence
+  // placement of newly loaded nets into recycled slots (k_place_*): slots
+  // taken from each ring and the ring positions they start at
+  unsigned long long place_ka, place_kv, place_ah, place_vh;
 };
 
 // Published step word of the persistent kernel.
@@ -82,6 +85,7 @@ struct Dev {
   unsigned long long* qseq;  // asynchronous kernel: sequence number of each ticket queue cell
   uint32_t* afree;
   uint32_t* vfree;
+  uint32_t* vown;        // net owning each name slot in use (kNoNet when free); NULL: not kept
   unsigned long long* netctr;
   int32_t* netstat;
   uint32_t* netrep;      // 1 once inet_net_finished reported the net
@@ -375,6 +379,7 @@ __device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t,
     if (old == kEmpty) return false;
     // second arrival: the slot is finished; clear it and free it
     __stcg(d.var + x, kEmpty);
+    if (d.vown) __stcg(d.vown + x, kNoNet);
     const int pos = atomicAdd(&s.misc[M_NVSTAGE], 1);
     if (pos < kVarStage * (int)blockDim.x) {
       s.vstage[pos] = x;
@@ -533,6 +538,7 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
         if (k < tv) x = s.lv[lv0 + k];
         else x = pool_slot(d.vfree, d.cap_vars, s.warp[W_VRING], (uint32_t)s.warp[W_VAVAIL], s.warp[W_VBUMP], k - tv);
         if (x >= d.cap_vars) in_range = false;
+        else if (d.vown) __stcg(d.vown + x, net);
         vals[(kValFresh + v) * B] = mk_var(x);
       }
     }
@@ -641,6 +647,7 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
       for (uint32_t f = 0; f < free_a; f++) {
         const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
         const uint32_t k = of + f;
+        __stcg(&d.node[slot].head, kFreeHead);
         if (k < keep) s.la[base0 + k] = slot;
         else __stcg(d.afree + (s.warp[W_AFREE] + (k - keep)) % d.cap_agents, slot);
       }

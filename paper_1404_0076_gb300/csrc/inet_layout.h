@@ -41,6 +41,15 @@ constexpr uint32_t kMaxIndex = (1u << 30) - 1;
 constexpr uint32_t kMaxLabels = 64;   // rule table is kMaxLabels^2 int16 in shared memory
 constexpr uint32_t kMaxNetSlots = (1u << 24) - 1;
 
+// Head word of a free agent slot: label 0xFF and net 0xFFFFFF, neither of
+// which a live agent can carry (labels < kMaxLabels, nets < kMaxNetSlots).
+// Every path that frees an agent slot writes it, so a scan of the arena
+// tells live agents (and their net) from free slots.
+constexpr int32_t kFreeHead = -1;
+// Owner word of a free name slot (the owner array holds the net of every
+// name slot in use).
+constexpr uint32_t kNoNet = 0xFFFFFFFFu;
+
 struct alignas(16) Node {
   int32_t head;   // label | net << 8
   uint32_t aux[3];

@@ -144,6 +144,7 @@ __global__ void k_paper_merge(Dev d, const uint32_t* keys, const unsigned long l
     t = (uint32_t)(vals[i + 1] >> 32);
     u = (uint32_t)(vals[i] >> 32);
     atomicAdd(merged, 1u);
+    if (d.vown && k < d.cap_vars) __stcg(d.vown + k, kNoNet);
     const unsigned long long tp = atomicAdd(&c->v_tail, 1ull);
     __stcg(d.vfree + tp % d.cap_vars, k);
     if (is_agent(t) && is_agent(u)) {

@@ -1,22 +1,23 @@
 """Continuous-batching request loop over the evaluator's C ABI.
 
-Requests (one net each) are admitted as they arrive, while the arena they go
-to has room for them by an estimate of their footprint; every admitted net
-joins the frontier of the nets already in flight (inet_stage), and the
-device runs the asynchronous loop in bounded epochs (slice_us), between
-which finished nets are found (inet_net_finished, a device scan that
-reports each net once) and new ones admitted.
-The results of finished nets are read back on a second stream
-(inet_readback_nats_begin / _end) while the device keeps reducing the
-others, so a long readback walk never stalls the loop.  Requests therefore overlap on the device with
-whatever is in flight; each result is independent of the mix because nets
-share no agent and interactions are local (Sec. 2.1).
+Requests (one net each) are admitted as they arrive, while the arena has
+room for them by an estimate of their footprint; every admitted net joins
+the frontier of the nets already in flight (inet_stage), and the device runs
+the asynchronous loop in bounded epochs (slice_us), between which finished
+nets are found (inet_net_finished, a device scan that reports each net once)
+and new ones admitted.  The results of finished nets are read back on a
+second stream (inet_readback_nats_begin / _end) while the device keeps
+reducing the others, so a long readback walk never stalls the loop.
+Requests therefore overlap on the device with whatever is in flight; each
+result is independent of the mix because nets share no agent and
+interactions are local (Sec. 2.1).
 
-Memory: two arenas are used in turn.  New requests go to the active one
-while its estimated use fits; when it is full, admission switches to the
-other, which is reset first once its last request has finished (its
-arena then holds only results already read back).  No arena ever needs a
-scan to free a finished net.
+Memory: one arena.  A request's net is freed once its result has been read
+back (inet_free_nets returns its agent and name slots and its id), and later
+requests are placed into the freed slots, so a long request holds only its
+own memory.  Frees are batched (one scan of the arena frees many nets): when
+the nets waiting to be freed hold a sixteenth of the arena, when net ids run
+short, or when a request does not fit.
 """
 from __future__ import annotations
 
@@ -53,134 +54,143 @@ class Server:
     def __init__(self, rules: str, device: int = 0, budget_bytes: int = 2 << 30, epoch_us: int = 1000,
                  max_nets: int = 1 << 15, max_pairs: int = 1 << 22, block: int = 0, grid: int = 0,
                  footprint=default_footprint, make_evaluator=None):
-        share = budget_bytes // 2
-        # per agent slot: 16-byte record + 4-byte ring entry; per name slot: 4 + 4;
-        # frontier: 2 x 8 bytes per pair
-        rest = max(share - 16 * max_pairs, 1 << 20)
+        # per agent slot: 16-byte record + 4-byte ring entry; per name slot:
+        # 4 (slot) + 4 (ring entry) + 4 (owner); per pair: 2 x 8 frontier + 8 sequence
+        rest = max(budget_bytes - 24 * max_pairs, 1 << 20)
         self.max_agents = int(min(rest * 3 // 4 // 20, (1 << 30) - 1))
-        self.max_vars = int(min(rest // 4 // 8, (1 << 30) - 1))
+        self.max_vars = int(min(rest // 4 // 12, (1 << 30) - 1))
         if make_evaluator is None:
             from . import Evaluator
 
             def make_evaluator():
                 return Evaluator(device, max_agents=self.max_agents, max_vars=self.max_vars,
                                  max_pairs=max_pairs, max_nets=max_nets)
-        self.ctx = [make_evaluator(), make_evaluator()]
-        for ev in self.ctx:
-            ev.load_rules(rules)
+        self.ev = make_evaluator()
+        self.ev.load_rules(rules)
         self.max_nets = max_nets
         self.epoch_us = epoch_us
         self.block, self.grid = block, grid
         self.footprint = footprint
-        self.active = 0
-        self.used = [0, 0]          # estimated agent slots committed per arena
-        self.nets = [0, 0]          # nets loaded per arena since its reset
-        self.inflight = [{}, {}]    # arena -> {net id: (rid, arrival, admitted)}
-        self.unstaged = [[], []]    # admitted nets not yet handed to the device
-        self.running = [0, 0]       # admitted nets not finished yet
-        self.done_nets = [set(), set()]  # finished, waiting for or in a readback
-        self.ready = [[], []]       # finished, readback not yet begun
-        self.rb_batch = [None, None]  # nets of the readback in flight
+        self.used = 0               # estimated agent slots of admitted nets not freed yet
+        self.inflight = {}          # net id -> (rid, arrival, admitted, need)
+        self.unstaged = []          # admitted nets not yet handed to the device
+        self.running = 0            # admitted nets not finished yet
+        self.ready = []             # finished, readback not yet begun
+        self.rb_batch = None        # nets of the readback in flight
+        self.to_free = []           # read back, waiting to be freed
+        self.free_need = 0          # their estimated slots
         self.epochs = 0
-        self.switches = 0
+        self.frees = 0              # inet_free_nets calls
+        self.freed = 0              # nets freed
+        self.resets = 0             # fatal errors (the arena is reset)
 
     def close(self):
-        for ev in self.ctx:
-            ev.close()
+        self.ev.close()
 
     # -- admission -------------------------------------------------------
-    def _room(self, k: int, need: int) -> bool:
-        return self.used[k] + need <= self.max_agents and self.nets[k] < self.max_nets
+    def _room(self, need: int) -> bool:
+        return self.used + need <= self.max_agents and len(self.inflight) + len(self.to_free) < self.max_nets
 
-    def _reset(self, k: int):
-        self.ctx[k].reset()
-        self.used[k] = 0
-        self.nets[k] = 0
-        self.unstaged[k] = []
-        self.running[k] = 0
-        self.done_nets[k] = set()
-        self.ready[k] = []
-        self.rb_batch[k] = None
+    def _free(self):
+        """Frees every net read back so far (one scan of the arena per call)."""
+        while self.to_free:
+            batch, self.to_free = self.to_free[:65536], self.to_free[65536:]
+            self.ev.free(batch)
+            self.frees += 1
+            self.freed += len(batch)
+        self.used -= self.free_need
+        self.free_need = 0
 
     def try_admit(self, rid: int, text: str, size: int, arrival: float, now: float) -> bool:
         need = self.footprint(text, size)
         if need > self.max_agents:
-            raise ValueError(f"request {rid} needs about {need} agent slots; an arena holds {self.max_agents}")
-        k = self.active
-        if not self._room(k, need):
-            other = 1 - k
-            if self.inflight[other]:
-                return False                      # both arenas busy: wait
-            self._reset(other)
-            self.active = k = other
-            self.switches += 1
-        ev = self.ctx[k]
-        nid = ev.load_net(text)
-        self.unstaged[k].append(nid)
-        self.used[k] += need
-        self.nets[k] += 1
-        self.inflight[k][nid] = (rid, arrival, now)
-        self.running[k] += 1
+            raise ValueError(f"request {rid} needs about {need} agent slots; the arena holds {self.max_agents}")
+        if not self._room(need) and self.to_free:
+            self._free()
+        if not self._room(need):
+            return False                          # wait for running requests to finish
+        nid = self.ev.load_net(text)
+        self.unstaged.append(nid)
+        self.used += need
+        self.inflight[nid] = (rid, arrival, now, need)
+        self.running += 1
         return True
 
     # -- device epochs and harvest ------------------------------------------
     def epoch(self, now_fn) -> list[Finished]:
         done = []
+        ev = self.ev
+        if self.unstaged:
+            ev.stage(self.unstaged)   # one upload for every net admitted since
+            self.unstaged = []
         reduced = False
-        for k in (0, 1):
-            ev = self.ctx[k]
-            if self.unstaged[k]:
-                ev.stage(self.unstaged[k])   # one upload for every net admitted since
-                self.unstaged[k] = []
-            if self.running[k]:
-                st = ev.reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
-                               check=False)
-                self.epochs += 1
-                reduced = True
-                if st["status"] not in ("OK", "STEP_LIMIT", "NO_RULE"):
-                    # a fatal error poisons the arena: every request in it fails
-                    t = now_fn()
-                    for nid in list(self.inflight[k]):
-                        rid, arr, adm = self.inflight[k].pop(nid)
-                        done.append(Finished(rid, arr, adm, t, None, 0, st["status"]))
-                    self._reset(k)
-                    continue
-                fin = [nid for nid in ev.finished() if nid in self.inflight[k]]
-                self.running[k] -= len(fin)
-                self.ready[k].extend(fin)
-                self.done_nets[k].update(fin)
-            done.extend(self._harvest(k, now_fn, wait=False))
-        if not reduced and any(b is not None for b in self.rb_batch):
-            time.sleep(50e-6)   # only readbacks in flight: poll gently
+        if self.running:
+            st = ev.reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
+                           check=False)
+            self.epochs += 1
+            reduced = True
+            if st["status"] not in ("OK", "STEP_LIMIT", "NO_RULE"):
+                # a fatal error poisons the arena: every request in it fails
+                t = now_fn()
+                for nid, (rid, arr, adm, _) in self.inflight.items():
+                    done.append(Finished(rid, arr, adm, t, None, 0, st["status"]))
+                self._reset()
+                return done
+            fin = [nid for nid in ev.finished() if nid in self.inflight]
+            self.running -= len(fin)
+            self.ready.extend(fin)
+        done.extend(self._harvest(now_fn, wait=False))
+        if self.to_free and (self.free_need * 16 >= self.max_agents or len(self.to_free) * 4 >= self.max_nets):
+            self._free()
+        if not reduced and self.rb_batch is not None:
+            time.sleep(50e-6)   # only a readback in flight: poll gently
         return done
 
-    def _harvest(self, k: int, now_fn, wait: bool) -> list[Finished]:
+    def _reset(self):
+        if self.rb_batch is not None:
+            self.ev.readback_nats_end(True)
+        self.ev.reset()
+        self.resets += 1
+        self.used = 0
+        self.inflight = {}
+        self.unstaged = []
+        self.running = 0
+        self.ready = []
+        self.rb_batch = None
+        self.to_free = []
+        self.free_need = 0
+
+    def _harvest(self, now_fn, wait: bool) -> list[Finished]:
         """Completes the readback in flight (if done) and begins the next."""
         out = []
-        ev = self.ctx[k]
-        if self.rb_batch[k] is not None:
+        ev = self.ev
+        if self.rb_batch is not None:
             r = ev.readback_nats_end(wait)
             if r is None:
                 return out
             vals, ints = r
             t = now_fn()
-            for nid, v, n in zip(self.rb_batch[k], vals, ints):
-                rid, arr, adm = self.inflight[k].pop(nid)
-                self.done_nets[k].discard(nid)
+            for nid, v, n in zip(self.rb_batch, vals, ints):
+                rid, arr, adm, need = self.inflight.pop(nid)
+                self.to_free.append(nid)
+                self.free_need += need
                 out.append(Finished(rid, arr, adm, t, v, n))
-            self.rb_batch[k] = None
-        if self.ready[k]:
-            batch, self.ready[k] = self.ready[k][:65536], self.ready[k][65536:]
+            self.rb_batch = None
+        if self.ready:
+            batch, self.ready = self.ready[:65536], self.ready[65536:]
             ev.readback_nats_begin(batch)
-            self.rb_batch[k] = batch
+            self.rb_batch = batch
         return out
 
     def busy(self) -> bool:
-        return bool(self.inflight[0] or self.inflight[1])
+        return bool(self.inflight)
 
-    def serve(self, requests, time_scale: float = 1.0, max_wall_s: float = math.inf) -> list[Finished]:
+    def serve(self, requests, time_scale: float = 1.0, max_wall_s: float = math.inf,
+              on_queue_empty=None) -> list[Finished]:
         """Runs `requests` (objects with .arrival_s, .net, .size) to the end.
-        Arrivals are replayed on the wall clock, scaled by time_scale."""
+        Arrivals are replayed on the wall clock, scaled by time_scale.
+        on_queue_empty(t, done), if given, is called once, the first time
+        every request has arrived and been admitted."""
         reqs = sorted(enumerate(requests), key=lambda ir: ir[1].arrival_s)
         pending = collections.deque(reqs)
         t0 = time.perf_counter()
@@ -201,10 +211,15 @@ class Server:
                 if not self.try_admit(rid, r.net, r.size, r.arrival_s * time_scale, now()):
                     break
                 waiting.popleft()
+            if on_queue_empty is not None and not pending and not waiting:
+                on_queue_empty(now(), list(out))
+                on_queue_empty = None
             if self.busy():
                 out.extend(self.epoch(now))
             elif pending and not waiting:
                 time.sleep(max(0.0, min(0.001, pending[0][1].arrival_s * time_scale - now())))
+        if self.to_free:
+            self._free()
         return out
 
 

@@ -1,6 +1,6 @@
 """The continuous-batching request loop (paper_1404_0076_gb300/serve.py).
 
-CPU: the admission and arena-switching logic against a fake evaluator.
+CPU: the admission and freeing logic against a fake evaluator.
 GPU: a stream of mixed requests whose results, computed while they overlap
 on the device, must equal each request reduced alone (the oracle).
 """
@@ -21,27 +21,42 @@ class Req:
 
 
 class FakeEvaluator:
-    """Completes each net after `size` epochs; counts resets."""
+    """Completes each net after `size` epochs; reuses freed ids like the
+    library; counts resets and the most nets held at once."""
 
     def __init__(self):
         self.left = {}
         self.value = {}
         self.next_id = 0
+        self.free_ids = []
         self.resets = 0
         self.staged = set()
         self.batch = None
         self.reported = set()
+        self.held_max = 0
 
     def load_rules(self, text):
         pass
 
     def load_net(self, text):
-        i = self.next_id
-        self.next_id += 1
+        if self.free_ids:
+            i = self.free_ids.pop()
+        else:
+            i = self.next_id
+            self.next_id += 1
         size = int(text.split(":")[1])
         self.left[i] = size
         self.value[i] = size * 10
+        self.held_max = max(self.held_max, len(self.left))
         return i
+
+    def free(self, ids):
+        for i in ids:
+            assert self.left[i] == 0 and i not in (self.batch or [])
+            del self.left[i], self.value[i]
+            self.staged.discard(i)
+            self.reported.discard(i)
+            self.free_ids.append(i)
 
     def stage(self, ids):
         self.staged.update(ids)
@@ -91,7 +106,7 @@ class FakeEvaluator:
         pass
 
 
-def test_admission_and_arena_switching_on_cpu():
+def test_admission_and_freeing_on_cpu():
     fakes = []
 
     def make():
@@ -101,7 +116,7 @@ def test_admission_and_arena_switching_on_cpu():
 
     srv = Server("", budget_bytes=64 << 20, max_pairs=1 << 10, make_evaluator=make,
                  footprint=lambda text, size: 10_000)
-    cap = srv.max_agents // 10_000          # requests one arena admits
+    cap = srv.max_agents // 10_000          # requests the arena admits at once
     assert cap >= 2
     reqs = [Req(0.0, f"net:{1 + (i % 5)}", 1 + (i % 5)) for i in range(4 * cap + 3)]
     done = srv.serve(reqs)
@@ -111,8 +126,11 @@ def test_admission_and_arena_switching_on_cpu():
         size = 1 + (d.rid % 5)
         assert d.value == 10 * size and d.interactions == size
         assert d.finished >= d.admitted >= d.arrival >= 0
-    assert srv.switches >= 2
-    assert sum(f.resets for f in fakes) >= 2
+    # one arena, never reset: finished nets were freed and their ids reused
+    assert len(fakes) == 1 and fakes[0].resets == 0
+    assert srv.frees >= 2 and srv.freed == len(reqs)
+    assert fakes[0].held_max <= cap and fakes[0].next_id <= cap
+    assert srv.used == 0 and not fakes[0].left
     s = summarize(done, 1.0)
     assert s["requests"] == len(reqs) and s["p99_ms"] >= s["p50_ms"]
 
@@ -150,24 +168,28 @@ def mixed_requests(n, seed=14040076 + 4):
 def test_results_in_the_mix_equal_results_alone(oracle):
     reqs = mixed_requests(600)
     # an arena holding about a quarter of the stream's estimated footprint
-    # forces several arena switches while requests overlap
+    # makes requests wait for the memory of finished ones, which is freed
+    # while others are in flight
     total = sum(default_footprint(r.net, r.size) for r in reqs)
     max_pairs = 1 << 16
     per_arena = max(total // 4, 4 * max(default_footprint(r.net, r.size) for r in reqs))
-    budget = 2 * (per_arena * 80 // 3 + 16 * max_pairs)
+    budget = per_arena * 80 // 3 + 24 * max_pairs
     srv = Server(W.ARITH_RULES, budget_bytes=budget, epoch_us=300, max_pairs=max_pairs)
     assert srv.max_agents < total // 2
     try:
         done = srv.serve(reqs)
+        use = srv.ev.arena_usage()
     finally:
         srv.close()
+    assert srv.frees >= 2 and srv.resets == 0
+    # the arena's bump pointer never passed its capacity: freed slots were reused
+    assert use["agent_slots"] <= srv.max_agents and use["live_agents"] == 0
     assert len(done) == len(reqs)
     alone = oracle.run(W.ARITH_RULES, [r.net for r in reqs], quiet=True, threads=8)
     for d in sorted(done, key=lambda d: d.rid):
         o = alone[d.rid]
         assert d.status == "OK"
         assert (d.value, d.interactions) == (o["nat"], o["interactions"]), d.rid
-    assert srv.switches >= 1
     # requests overlapped on the device: some request was admitted while
     # another one was still in flight
     spans = sorted((d.admitted, d.finished) for d in done)
