@@ -299,14 +299,24 @@ inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n);
 /* inet_free_nets() for one net. */
 inet_status inet_free_net(inet_ctx* ctx, int32_t net_id);
 
-/* How much of the arena is in use: *agent_slots_out and *name_slots_out get
- * the bump pointers (slots handed out at least once since the last reset;
- * each slot below them is live or waits in a free ring), *live_agents_out the
- * agents alive in all nets.  Loaded nets are uploaded and placed first, so
- * the figures include them.  Any pointer may be NULL.  The paper has no
- * counterpart: it lets a request loop see that freed memory is reused. */
-inet_status inet_arena_usage(inet_ctx* ctx, uint64_t* agent_slots_out, uint64_t* name_slots_out,
-                             int64_t* live_agents_out);
+/* How much of the arena is in use (inet_arena_usage). */
+typedef struct inet_arena_usage_t {
+  uint64_t agent_slots;       /* agent bump pointer: slots handed out at least once since the
+                                 last reset; each slot below it is live or waits in a free ring */
+  uint64_t name_slots;        /* name bump pointer, likewise */
+  uint64_t free_agent_slots;  /* agent slots waiting in the free ring */
+  uint64_t free_name_slots;   /* name slots waiting in the free ring */
+  int64_t live_agents;        /* agents alive in all nets */
+  uint32_t nets;              /* net ids in use */
+  uint32_t free_net_ids;      /* ids released by inet_free_nets, not reused yet */
+} inet_arena_usage_t;
+
+/* Fills *out.  Loaded nets are uploaded and placed first, so the figures
+ * include them.  Between reductions every free slot is in a ring, so
+ * agent_slots - free_agent_slots slots are held by nets (likewise for
+ * names).  The paper has no counterpart: it lets a request loop see that
+ * freed memory is reused. */
+inet_status inet_arena_usage(inet_ctx* ctx, inet_arena_usage_t* out);
 
 /* Per-net counters; live and residual agents come from the readback
  * snapshot. */

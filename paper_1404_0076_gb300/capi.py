@@ -79,6 +79,12 @@ class inet_rule_desc(C.Structure):
                 ("n_new", C.c_int32), ("new_ports", C.c_int32), ("n_fresh", C.c_int32), ("n_link", C.c_int32)]
 
 
+class inet_arena_usage_t(C.Structure):
+    _fields_ = [("agent_slots", C.c_uint64), ("name_slots", C.c_uint64), ("free_agent_slots", C.c_uint64),
+                ("free_name_slots", C.c_uint64), ("live_agents", C.c_int64), ("nets", C.c_uint32),
+                ("free_net_ids", C.c_uint32)]
+
+
 class InetError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -105,7 +111,7 @@ def _load():
         "inet_stage": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_nets": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_net": ([P, C.c_int32], C.c_int32),
-        "inet_arena_usage": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_int64)], C.c_int32),
+        "inet_arena_usage": ([P, C.POINTER(inet_arena_usage_t)], C.c_int32),
         "inet_transfer_bytes": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
         "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
@@ -238,9 +244,9 @@ def inet_free_net(ctx, net_id: int) -> None:
 
 
 def inet_arena_usage(ctx) -> dict:
-    a, v, live = C.c_uint64(), C.c_uint64(), C.c_int64()
-    _check(ctx, LIB.inet_arena_usage(ctx, C.byref(a), C.byref(v), C.byref(live)))
-    return {"agent_slots": a.value, "name_slots": v.value, "live_agents": live.value}
+    u = inet_arena_usage_t()
+    _check(ctx, LIB.inet_arena_usage(ctx, C.byref(u)))
+    return {k: getattr(u, k) for k, _ in u._fields_}
 
 
 def inet_transfer_bytes(ctx) -> tuple[int, int]:

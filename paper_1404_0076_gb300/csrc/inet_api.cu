@@ -1522,17 +1522,30 @@ inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
 
 inet_status inet_free_net(inet_ctx* ctx, int32_t net_id) { return inet_free_nets(ctx, &net_id, 1); }
 
-inet_status inet_arena_usage(inet_ctx* ctx, uint64_t* agent_slots_out, uint64_t* name_slots_out,
-                             int64_t* live_agents_out) {
-  if (!ctx) return INET_ERR_INVALID_ARG;
+inet_status inet_arena_usage(inet_ctx* ctx, inet_arena_usage_t* out) {
+  if (!ctx || !out) return INET_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
   if (!ctx->host_only && ctx->ws_ready) {
     DeviceGuard g(ctx->device);
     inet_status s = upload_staged(ctx);
     if (s) return s;
+    static thread_local unsigned long long hr[6];  // a_head, a_tail, a_pub, v_head, v_tail, v_pub
+    CK(d2h(ctx, &hr[0], &ctx->dev.ctrl->a_head, 8));
+    CK(d2h(ctx, &hr[1], &ctx->dev.ctrl->a_tail, 8));
+    CK(d2h(ctx, &hr[2], &ctx->dev.ctrl->a_pub, 8));
+    CK(d2h(ctx, &hr[3], &ctx->dev.ctrl->v_head, 8));
+    CK(d2h(ctx, &hr[4], &ctx->dev.ctrl->v_tail, 8));
+    CK(d2h(ctx, &hr[5], &ctx->dev.ctrl->v_pub, 8));
+    CK(cudaStreamSynchronize(ctx->stream));
+    // a pop that found the ring empty advanced the head past the published end
+    out->free_agent_slots = hr[1] - std::min(hr[0], hr[2]);
+    out->free_name_slots = hr[4] - std::min(hr[3], hr[5]);
   }
-  if (agent_slots_out) *agent_slots_out = ctx->a_bump;
-  if (name_slots_out) *name_slots_out = ctx->v_bump;
-  if (live_agents_out) *live_agents_out = ctx->live;
+  out->agent_slots = ctx->a_bump;
+  out->name_slots = ctx->v_bump;
+  out->live_agents = ctx->live;
+  out->nets = (uint32_t)(ctx->nets.size() - ctx->free_net_ids.size());
+  out->free_net_ids = (uint32_t)ctx->free_net_ids.size();
   return INET_OK;
 }
 

@@ -733,7 +733,9 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
       }
     }
   }
-  // free slots known only to this warp go back to the rings
+  // free slots known only to this warp go back to the rings, marked free:
+  // a stack also holds slots fetched from the pools and never used, which
+  // may come fresh from the bump pointer with stale contents
   __syncwarp();
   {
     unsigned long long ab = 0, vb = 0;
@@ -743,8 +745,16 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
     }
     ab = __shfl_sync(kFull, ab, 0);
     vb = __shfl_sync(kFull, vb, 0);
-    for (int j = lane; j < S.ac; j += 32) __stcg(d.afree + (ab + j) % d.cap_agents, W.astk[j]);
-    for (int j = lane; j < S.vc; j += 32) __stcg(d.vfree + (vb + j) % d.cap_vars, W.vstk[j]);
+    for (int j = lane; j < S.ac; j += 32) {
+      const uint32_t sl = W.astk[j];
+      if (sl < d.cap_agents) __stcg(&d.node[sl].head, kFreeHead);
+      __stcg(d.afree + (ab + j) % d.cap_agents, sl);
+    }
+    for (int j = lane; j < S.vc; j += 32) {
+      const uint32_t x = W.vstk[j];
+      if (d.vown && x < d.cap_vars) __stcg(d.vown + x, kNoNet);
+      __stcg(d.vfree + (vb + j) % d.cap_vars, x);
+    }
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < d.n_tmpl; i += blockDim.x)

@@ -242,7 +242,8 @@ def test_argument_errors_are_reported_not_crashed(capi):
     assert L.inet_free_nets(None, bad, 1) == capi.INET_ERR_INVALID_ARG
     assert L.inet_free_nets(ctx, bad, 0) == capi.INET_ERR_NO_DEVICE
     assert L.inet_free_net(ctx, 7) == capi.INET_ERR_NO_DEVICE
-    assert L.inet_arena_usage(None, None, None, None) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_arena_usage(None, None) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_arena_usage(ctx, None) == capi.INET_ERR_INVALID_ARG
     assert L.inet_control_link(0, None, 0, 0, 7, None, 0, out, None, None) == capi.INET_ERR_INVALID_ARG
     assert L.inet_bench_exch(0, 0, 0, None) == capi.INET_ERR_INVALID_ARG
 
@@ -250,10 +251,12 @@ def test_argument_errors_are_reported_not_crashed(capi):
 def test_arena_usage_counts_loaded_nets(capi):
     ctx = host_ctx(capi)
     capi.inet_load_rules(ctx, W.ARITH_RULES)
-    assert capi.inet_arena_usage(ctx) == {"agent_slots": 0, "name_slots": 0, "live_agents": 0}
+    zero = {"agent_slots": 0, "name_slots": 0, "free_agent_slots": 0, "free_name_slots": 0, "live_agents": 0,
+            "nets": 0, "free_net_ids": 0}
+    assert capi.inet_arena_usage(ctx) == zero
     capi.inet_load_net(ctx, W.add_net(3, 2))        # Add, S^3 Z, S^2 Z: 8 agents; the name r
     capi.inet_load_nets(ctx, [W.add_net(0, 0)] * 2)
-    assert capi.inet_arena_usage(ctx) == {"agent_slots": 8 + 2 * 3, "name_slots": 3, "live_agents": 14}
+    assert capi.inet_arena_usage(ctx) == dict(zero, agent_slots=8 + 2 * 3, name_slots=3, live_agents=14, nets=3)
 
 
 def test_reduce_refuses_bad_modes_and_shapes(capi):

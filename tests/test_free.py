@@ -54,23 +54,25 @@ def test_freed_slots_are_reused_and_results_stay_exact(orc, mode):
     for rnd in range(4):
         ids = ev.load_nets(nets)
         id_sets.append(set(ids))
-        # one block in the persistent form: the allocation order repeats
-        # exactly, so a round that starts with every slot of the last one in
-        # the rings never takes a never-used slot
-        kw = dict(grid=1) if mode == "persistent" else {}
-        ev.reduce(ids, mode=mode, **kw)
+        ev.reduce(ids, mode=mode)
         check_against(ev, ids, expect)
         use = ev.arena_usage()
+        slack = 4 if mode == "async" else 16     # the async driver's allocation order varies most
         if first is None:
             first = use
-        elif mode == "persistent":
-            assert use["agent_slots"] == first["agent_slots"] and use["name_slots"] == first["name_slots"], (rnd, use)
         else:
-            assert use["agent_slots"] <= first["agent_slots"] * 5 // 4 + 64, (rnd, use, first)
-            assert use["name_slots"] <= first["name_slots"] * 5 // 4 + 64, (rnd, use, first)
+            # the round before left every slot in the rings; the bump
+            # pointers grow by at most a small share (how many slots each
+            # step takes from the rings before freed ones are published varies
+            # with the order pairs are handed out), never by a round's worth
+            assert use["agent_slots"] <= first["agent_slots"] + first["agent_slots"] // slack + 64, (rnd, use, first)
+            assert use["name_slots"] <= first["name_slots"] + first["name_slots"] // slack + 64, (rnd, use, first)
         assert use["live_agents"] == sum(o["live"] for o in expect)
         ev.free(ids)
-        assert ev.arena_usage()["live_agents"] == 0
+        use = ev.arena_usage()
+        # nothing leaks: every slot below the bump pointers is back in a ring
+        assert use["live_agents"] == 0 and use["nets"] == 0, use
+        assert use["free_agent_slots"] == use["agent_slots"] and use["free_name_slots"] == use["name_slots"], use
     # every round reused the ids the previous one released
     assert all(s == id_sets[0] for s in id_sets)
     ev.close()
@@ -126,6 +128,10 @@ def test_free_while_other_nets_reduce(orc):
     capi.inet_destroy(h)
     assert len(usage) >= 2
     assert usage[-1] <= usage[0] + 5 * one_batch, (usage, one_batch)
+    ev.free(lid)
+    use = ev.arena_usage()
+    assert use["live_agents"] == 0 and use["nets"] == 0, use
+    assert use["free_agent_slots"] == use["agent_slots"] and use["free_name_slots"] == use["name_slots"], use
     ev.close()
 
 

@@ -220,10 +220,14 @@ def test_requests_shard_over_devices_on_cpu():
     for d in done:
         size = 1 + (d.rid % 7)
         assert d.value == 10 * size and d.interactions == size
-    # every device got work, and the routing kept their totals close
+    # every device got work (how much depends on how fast each serving
+    # thread reports completions), and every request's load was returned
     assert all(n > 0 for n in ms.routed) and sum(ms.routed) == 300
-    assert max(ms.routed) - min(ms.routed) <= 100
     assert ms.load == [0, 0, 0]
+    # the routing itself: an arrival goes to the least loaded device
+    ms.load = [50, 7, 20]
+    assert ms.route("net:5", 5) == 1 and ms.load == [50, 12, 20]
+    assert ms.route("net:9", 9) == 1 and ms.route("net:1", 1) == 2
     ms.close()
 
 
