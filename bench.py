@@ -236,13 +236,16 @@ def expected_value(r) -> int:
 
 
 def serving_leg(args, local: int) -> dict:
-    """Continuous batching on the serving mix: the first --serve-requests
-    requests of the 100k-request Poisson stream.  First all at once
-    (saturated), which measures the serving capacity C in interactions/s;
-    then replayed on the wall clock at load rho of C (arrival rate
-    rho * C / mean request size) for rho in 0.5, 0.8, 0.95, and at the
-    stream's own 1000 requests/s.  Every result is checked against its
-    closed form (value and exact interaction count)."""
+    """Continuous batching on the serving mix: the 100k-request Poisson
+    stream (--serve-requests takes its first requests only).  First every
+    request arrives at once (saturated): the serving capacity C is the rate
+    of interactions the device performs while admission still has a
+    backlog (the queue of arrived requests never empties in that window),
+    not the wall time of the whole run, which the longest request's chain of
+    dependent interactions sets.  Then the stream is replayed on the wall
+    clock at load rho of C (arrival rate rho * C / mean request size) for
+    each rho of --serve-rhos.  Every result is checked against its closed
+    form (value and exact interaction count)."""
     import dataclasses
 
     from paper_1404_0076_gb300.serve import Server, summarize
@@ -254,37 +257,106 @@ def serving_leg(args, local: int) -> dict:
     out = {"workload": "serving mix: Poisson arrivals, one net each from add/mul/ack/fib, sizes lognormal "
                        "(median 1e3 interactions, sigma 2.16, clipped to 1e7), seed 14040076+4",
            "requests": len(reqs), "mean_request_interactions": mean_size, "budget_bytes": budget, "arenas": 1,
-           "epoch_us": args.serve_epoch_us, "sample": f"first {len(reqs)} of the 100000-request stream"}
+           "largest_request_interactions": max(r.size for r in reqs),
+           "epoch_us": args.serve_epoch_us,
+           "sample": "the whole 100000-request stream" if len(reqs) == 100000
+           else f"first {len(reqs)} of the 100000-request stream"}
 
-    def run(scale: float) -> dict:
-        e0, s0, n0 = srv.epochs, srv.frees, srv.freed
+    def run(scale: float, sample=None) -> dict:
+        rr = reqs if sample is None else reqs[:sample]
+        e0, s0, n0, p0 = srv.epochs, srv.frees, srv.freed, srv.performed
+        h0 = dict(srv.host_s)
+        win = {}
+
+        def queue_empty(t, done_so_far):
+            win["t"] = t
+            win["performed"] = srv.performed - p0
+            win["completed"] = len(done_so_far)
+
         t0 = time.perf_counter()
-        done = srv.serve(reqs, time_scale=scale)
+        done = srv.serve(rr, time_scale=scale, on_queue_empty=queue_empty)
         wall = time.perf_counter() - t0
         rec = summarize(done, wall)
         rec.update(wall_s=wall, epochs=srv.epochs - e0, free_calls=srv.frees - s0, nets_freed=srv.freed - n0,
-                   arena_switches=0,
+                   device_interactions=srv.performed - p0,
+                   host_s={k: round(v - h0.get(k, 0.0), 3) for k, v in srv.host_s.items()},
+                   largest_served=max((rr[d.rid].size for d in done if d.status == "OK"), default=0),
                    wrong=sum(1 for d in done if d.status != "OK"
-                             or (d.value, d.interactions) != (expect[d.rid], reqs[d.rid].size)))
+                             or (d.value, d.interactions) != (expect[d.rid], rr[d.rid].size)))
+        if win:
+            rec["backlog_window_s"] = win["t"]
+            rec["backlog_interactions"] = win["performed"]
+            rec["backlog_completed"] = win["completed"]
         return rec
 
     try:
-        srv.serve([dataclasses.replace(r, arrival_s=0.0) for r in reqs[:64]])  # warm-up
-        out["saturated"] = run(0.0)
-        cap = out["saturated"]["interactions_per_s"]
+        srv.serve([dataclasses.replace(r, arrival_s=0.0) for r in reqs[:256]])  # warm-up
+        sat = run(0.0)
+        out["saturated"] = sat
+        # capacity: interactions performed per second while arrived requests
+        # were still waiting for admission (at least 0.5 s of backlog); else
+        # the whole run
+        if sat.get("backlog_window_s", 0) >= 0.5:
+            cap = sat["backlog_interactions"] / sat["backlog_window_s"]
+            out["capacity_how"] = "device interactions per second while the admission queue was non-empty " \
+                                  f"({sat['backlog_window_s']:.2f} s backlog of the saturated run)"
+        else:
+            cap = sat["device_interactions"] / sat["wall_s"]
+            out["capacity_how"] = "device interactions per second over the whole saturated run (no backlog)"
         out["capacity_interactions_per_s"] = cap
         rate0 = len(reqs) / reqs[-1].arrival_s          # the stream's own rate
-        for rho in (0.5, 0.8, 0.95):
+        for rho in args.serve_rhos:
             lam = rho * cap / mean_size                   # requests per second
-            rec = run(rate0 / lam)
+            rec = run(rate0 / lam, args.serve_rho_sample)
             rec["rho"], rec["requests_per_s"] = rho, lam
             out[f"rho_{rho}"] = rec
-        rec = run(1.0)
-        rec["requests_per_s"] = rate0
-        out["stream_rate"] = rec
     finally:
         srv.close()
     return out
+
+
+def narrow_leg(args, local: int, name: str) -> dict:
+    """A narrow-frontier workload (the paper's Fig. 2 regime): timed like
+    the headline, over --narrow-steps steps, in the form and launch shape
+    the autotuner picks, with its critical-path depth (steps of the
+    maximally parallel loop) and time per level."""
+    import torch
+
+    from paper_1404_0076_gb300 import Evaluator
+    from paper_1404_0076_gb300.autotune import Autotuner
+    nets, desc, caps, rules_text = workload(name)
+    ev = Evaluator(device=local, **caps)
+    ev.load_rules(rules_text)
+    props = torch.cuda.get_device_properties(local)
+    tuned = Autotuner().tune(ev, rules_text, nets, "auto", gpu=props.name, num_sms=props.multi_processor_count)
+    opts = dict(mode="async", block=0, grid=0, solo_max=0)
+    opts.update(tuned)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def prepared():
+        ev.reset()
+        ev.stage(ev.load_nets(nets))
+        flush.fill_(1)
+        torch.cuda.synchronize()
+
+    for _ in range(3):
+        prepared()
+        ev.reduce([], **opts)
+    ms, ints = [], 0
+    for _ in range(args.narrow_steps):
+        prepared()
+        st = ev.reduce([], **opts)
+        ms.append(st["device_ms"])
+        ints += st["interactions"]
+    prepared()
+    depth = ev.reduce([], mode="persistent")["steps"]
+    ev.close()
+    step_ms = sum(ms) / len(ms)
+    return {"workload": desc, "interactions_per_step": ints // args.narrow_steps,
+            "interactions_per_s": ints / (sum(ms) / 1e3), "ms_per_step": step_ms, "steps": args.narrow_steps,
+            "depth_levels": depth, "ns_per_level": 1e6 * step_ms / max(1, depth),
+            "mode": opts["mode"], "block": opts["block"] or 256, "grid": opts["grid"] or "auto",
+            "launch_shape": "autotuned"}
 
 
 # --- our arm ------------------------------------------------------------------------
@@ -306,7 +378,14 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--no-control", action="store_true", help="skip the sort-based linker control")
-    ap.add_argument("--serve-requests", type=int, default=6000)
+    ap.add_argument("--serve-requests", type=int, default=100000)
+    ap.add_argument("--serve-rhos", type=float, nargs="*", default=[0.5, 0.8, 0.95])
+    ap.add_argument("--serve-rho-sample", type=int, default=None,
+                    help="requests of the stream replayed at each rho (default: all)")
+    ap.add_argument("--no-narrow", action="store_true", help="skip the Ackermann and Fibonacci keys")
+    ap.add_argument("--narrow-steps", type=int, default=5)
+    ap.add_argument("--plain-sample", type=int, default=128,
+                    help="nets of the batch (every k-th) reduced one per launch by the host-driven loop")
     ap.add_argument("--serve-epoch-us", type=int, default=250)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     args = ap.parse_args()
@@ -466,7 +545,8 @@ def main():
         ids = prepared()
         stp = ev.reduce([], mode="plain")
         one = []
-        sample = nets[:16]
+        stride = max(1, len(nets) // max(1, args.plain_sample))
+        sample = nets[::stride][: args.plain_sample]
         for net in sample:
             ev.reset()
             i = ev.load_net(net)
@@ -478,7 +558,8 @@ def main():
                                                "Sec. 3.5 (own kernels), for comparison",
                  "batch_plain": stp["interactions"] / (stp["device_ms"] / 1e3),
                  "one_net_per_launch": sum(a for a, _ in one) / (sum(b for _, b in one) / 1e3),
-                 "one_net_sample": f"first {len(sample)} nets, each reduced alone by the host-driven loop",
+                 "one_net_sample": f"{len(sample)} nets (every {stride}th of the batch), each reduced alone by "
+                                   "the host-driven loop",
                  "unit": UNIT}
 
     cpu = None
@@ -513,6 +594,10 @@ def main():
                           "until no merge (method 1) vs one launch of atomic exchanges with chain chasing (method 0); "
                           "chains of 1 + Geometric(0.8) - 1 names; best of 3"}
 
+    narrow = None
+    if rank == 0 and world == 1 and not args.no_narrow:
+        narrow = {name: narrow_leg(args, local, name) for name in ("ack3", "fib")}
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_leg(args, local)
@@ -528,7 +613,8 @@ def main():
                            "l2": "flushed (256 MiB write) before every timed step",
                            "parallelism": f"independent batches, {world} rank(s)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "plain": plain, "serving": serving, "paper_com_control": control}
+                "clocks": clk.summary(), "plain": plain, "serving": serving, "paper_com_control": control,
+                "narrow_frontier": narrow}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -50,13 +50,6 @@
 #include <utility>
 #include <vector>
 
-// Planted-mistake hooks: tests compile mutants with -DORACLE_MUTANT=k to show
-// that the pins catch each mistake.  The default build (0) has none.
-#ifndef ORACLE_MUTANT
-#define ORACLE_MUTANT 0
-#endif
-#define MUTANT(k) (ORACLE_MUTANT == (k))
-
 namespace {
 
 constexpr int kMaxArity = 8;
@@ -397,7 +390,6 @@ struct Config {
     free_term(x1);
     free_term(x2);
     free_names.push_back(x);
-    if (MUTANT(7) && !is_name(u) && !is_name(t)) { add_eq(t, t); return true; }
     add_eq(t, u);
     return true;
   }
@@ -414,26 +406,22 @@ struct Config {
       throw std::runtime_error("NO_RULE: no rule for " + rs.sym.names[(size_t)l->sym] + " = " +
                                rs.sym.names[(size_t)r->sym]);
     int ridx = it->second / 2;
-    if ((it->second & 1) && !MUTANT(4)) std::swap(l, r);
+    if (it->second & 1) std::swap(l, r);
     const Rule& rule = rs.rules[(size_t)ridx];
     std::vector<Term*> bind((size_t)rule.nvars, nullptr);   // LHS names -> subterms
     std::vector<int64_t> fresh((size_t)rule.nvars, -1);     // bound names -> fresh names
     for (size_t i = 0; i < rule.a_vars.size(); i++)
-      bind[(size_t)rule.a_vars[i]] = MUTANT(1) ? l->arg[rule.a_vars.size() - 1 - i] : l->arg[i];
+      bind[(size_t)rule.a_vars[i]] = l->arg[i];
     for (size_t i = 0; i < rule.b_vars.size(); i++) bind[(size_t)rule.b_vars[i]] = r->arg[i];
-    int64_t shared = -1;
     for (int v = 0; v < rule.nvars; v++)
-      if (!rule.is_lhs[(size_t)v]) {
-        if (MUTANT(3) && shared >= 0) { fresh[(size_t)v] = shared; continue; }
-        fresh[(size_t)v] = shared = fresh_name();
-      }
+      if (!rule.is_lhs[(size_t)v]) fresh[(size_t)v] = fresh_name();
     std::vector<std::pair<Term*, Term*>> out;
     for (const auto& q : rule.rhs) out.emplace_back(inst(q.first, bind, fresh), inst(q.second, bind, fresh));
     free_term(l);
     free_term(r);
-    live += rule.rhs_agents - 2 + (MUTANT(6) && rule.rhs_agents > 2 ? 1 : 0);
+    live += rule.rhs_agents - 2;
     peak_live = std::max(peak_live, live);
-    if (!(MUTANT(2) && rule.rhs.empty())) interactions++;
+    interactions++;
     per_rule[(size_t)ridx]++;
     for (auto& q : out) add_eq(q.first, q.second);
   }
@@ -536,7 +524,6 @@ struct Config {
       free_term(xleaf);
       free_term(leaf);
       free_names.push_back(x);
-      if (MUTANT(5) && !is_name(t) && rs.sym.arity[(size_t)t->sym] > 0) t = t->arg[0];
       *slot = t;
       // t may now be a name that is a top-level side elsewhere: nothing to
       // register, since it now sits at a nested or interface position.

@@ -22,6 +22,7 @@ short, or when a request does not fit.
 from __future__ import annotations
 
 import collections
+import itertools
 import math
 import time
 from dataclasses import dataclass
@@ -83,6 +84,8 @@ class Server:
         self.frees = 0              # inet_free_nets calls
         self.freed = 0              # nets freed
         self.resets = 0             # fatal errors (the arena is reset)
+        self.performed = 0          # interactions the device performed (all epochs)
+        self.host_s = collections.Counter()   # wall time by phase: load, stage, reduce, finished, harvest, free
 
     def close(self):
         self.ev.close()
@@ -93,6 +96,7 @@ class Server:
 
     def _free(self):
         """Frees every net read back so far (one scan of the arena per call)."""
+        t0 = time.perf_counter()
         while self.to_free:
             batch, self.to_free = self.to_free[:65536], self.to_free[65536:]
             self.ev.free(batch)
@@ -100,33 +104,62 @@ class Server:
             self.freed += len(batch)
         self.used -= self.free_need
         self.free_need = 0
+        self.host_s["free"] += time.perf_counter() - t0
 
     def try_admit(self, rid: int, text: str, size: int, arrival: float, now: float) -> bool:
-        need = self.footprint(text, size)
-        if need > self.max_agents:
-            raise ValueError(f"request {rid} needs about {need} agent slots; the arena holds {self.max_agents}")
-        if not self._room(need) and self.to_free:
-            self._free()
-        if not self._room(need):
-            return False                          # wait for running requests to finish
-        nid = self.ev.load_net(text)
-        self.unstaged.append(nid)
-        self.used += need
-        self.inflight[nid] = (rid, arrival, now, need)
-        self.running += 1
-        return True
+        return self.admit_many([(rid, text, size, arrival)], now) == 1
+
+    def admit_many(self, reqs, now: float) -> int:
+        """Admits requests (rid, text, size, arrival) in order while they
+        fit; their texts are parsed together (inet_load_nets, on the host
+        thread pool).  Returns how many were admitted."""
+        take, needs = [], []
+        extra = 0
+
+        def fits(need):
+            return (self.used + extra + need <= self.max_agents and
+                    len(self.inflight) + len(self.to_free) + len(take) < self.max_nets)
+        for rid, text, size, arrival in reqs:
+            need = self.footprint(text, size)
+            if need > self.max_agents:
+                raise ValueError(f"request {rid} needs about {need} agent slots; the arena holds {self.max_agents}")
+            if not fits(need) and self.to_free:
+                self._free()
+            if not fits(need):
+                break                             # wait for running requests to finish
+            take.append((rid, text, size, arrival))
+            needs.append(need)
+            extra += need
+        if not take:
+            return 0
+        t0 = time.perf_counter()
+        nids = self.ev.load_nets([t for _, t, _, _ in take])
+        self.host_s["load"] += time.perf_counter() - t0
+        for (rid, _, _, arrival), need, nid in zip(take, needs, nids):
+            self.unstaged.append(nid)
+            self.used += need
+            self.inflight[nid] = (rid, arrival, now, need)
+            self.running += 1
+        return len(take)
 
     # -- device epochs and harvest ------------------------------------------
     def epoch(self, now_fn) -> list[Finished]:
         done = []
         ev = self.ev
+        clk = time.perf_counter
+        t0 = clk()
         if self.unstaged:
             ev.stage(self.unstaged)   # one upload for every net admitted since
             self.unstaged = []
+        t1 = clk()
+        self.host_s["stage"] += t1 - t0
         reduced = False
         if self.running:
             st = ev.reduce([], mode="async", slice_us=self.epoch_us, block=self.block, grid=self.grid,
                            check=False)
+            t2 = clk()
+            self.host_s["reduce"] += t2 - t1
+            self.performed += st.get("interactions", 0)
             self.epochs += 1
             reduced = True
             if st["status"] not in ("OK", "STEP_LIMIT", "NO_RULE"):
@@ -139,7 +172,10 @@ class Server:
             fin = [nid for nid in ev.finished() if nid in self.inflight]
             self.running -= len(fin)
             self.ready.extend(fin)
+            self.host_s["finished"] += clk() - t2
+        t3 = clk()
         done.extend(self._harvest(now_fn, wait=False))
+        self.host_s["harvest"] += clk() - t3
         if self.to_free and (self.free_need * 16 >= self.max_agents or len(self.to_free) * 4 >= self.max_nets):
             self._free()
         if not reduced and self.rb_batch is not None:
@@ -199,18 +235,22 @@ class Server:
             return time.perf_counter() - t0
 
         out: list[Finished] = []
-        waiting = collections.deque()
+        waiting = collections.deque()   # (rid, request, text); texts are built when first tried
         while pending or waiting or self.busy():
             t = now()
             if t > max_wall_s:
                 break
             while pending and pending[0][1].arrival_s * time_scale <= t:
-                waiting.append(pending.popleft())
-            while waiting:
-                rid, r = waiting[0]
-                if not self.try_admit(rid, r.net, r.size, r.arrival_s * time_scale, now()):
-                    break
-                waiting.popleft()
+                rid, r = pending.popleft()
+                waiting.append([rid, r, None])
+            if waiting:
+                batch = []
+                for w in itertools.islice(waiting, 4096):
+                    if w[2] is None:
+                        w[2] = w[1].net
+                    batch.append((w[0], w[2], w[1].size, w[1].arrival_s * time_scale))
+                for _ in range(self.admit_many(batch, now())):
+                    waiting.popleft()
             if on_queue_empty is not None and not pending and not waiting:
                 on_queue_empty(now(), list(out))
                 on_queue_empty = None

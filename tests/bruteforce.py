@@ -318,10 +318,17 @@ def canon_key(iface, eqs) -> str:
     return "|".join(out) + f"#{unreached}"
 
 
+def agents_in(t) -> int:
+    return 0 if is_name(t) else 1 + sum(agents_in(a) for a in t[2])
+
+
 def explore(rules_text: str, net_text: str, limit_states: int = 200000):
-    """All reduction orders from the net.  Returns (states, min_len, max_len,
-    finals, per-state-consistent) where finals is the set of rendered normal
-    forms and the lengths are numbers of ->int steps."""
+    """All reduction orders from the net.  Returns a dict: states, min / max
+    path length (->int steps), finals (the set of rendered normal forms),
+    consistent (every state's paths have one length), and peak_min /
+    peak_max: over all paths, the least and the greatest largest number of
+    live agents (agents anywhere in the interface and the equations) that a
+    path passes through."""
     rules, _ = parse_rules(rules_text)
     iface, eqs = parse_net(net_text)
     fresh = Fresh()
@@ -329,29 +336,35 @@ def explore(rules_text: str, net_text: str, limit_states: int = 200000):
     consistent = [True]
     sys.setrecursionlimit(max(10000, sys.getrecursionlimit()))
 
+    iface_agents = sum(agents_in(t) for t in iface)
+
     def go(eqs):
         key = canon_key(iface, eqs)
         if key in memo:
             return memo[key]
         if len(memo) > limit_states:
             raise RuntimeError("state space too large")
+        live = iface_agents + sum(agents_in(t) + agents_in(u) for t, u in eqs)
         active = [k for k, (t, u) in enumerate(eqs) if not is_name(t) and not is_name(u)]
         if not active:
             fi, fe = sub_col(iface, eqs)
-            res = (0, 0, frozenset([(render(fi), len(fe))]))
+            res = (0, 0, frozenset([(render(fi), len(fe))]), live, live)
         else:
-            lo, hi, fin = None, None, set()
+            lo, hi, fin, plo, phi = None, None, set(), None, None
             for k in active:
                 new, _ = interact(eqs, k, rules, fresh)
-                a, b, f = go(com_fixpoint(new))
+                a, b, f, pa, pb = go(com_fixpoint(new))
                 lo = a + 1 if lo is None else min(lo, a + 1)
                 hi = b + 1 if hi is None else max(hi, b + 1)
+                plo = pa if plo is None else min(plo, pa)
+                phi = pb if phi is None else max(phi, pb)
                 fin |= f
             if lo != hi:
                 consistent[0] = False
-            res = (lo, hi, frozenset(fin))
+            res = (lo, hi, frozenset(fin), max(live, plo), max(live, phi))
         memo[key] = res
         return res
 
-    lo, hi, fin = go(com_fixpoint(eqs))
-    return {"states": len(memo), "min": lo, "max": hi, "finals": fin, "consistent": consistent[0]}
+    lo, hi, fin, plo, phi = go(com_fixpoint(eqs))
+    return {"states": len(memo), "min": lo, "max": hi, "finals": fin, "consistent": consistent[0],
+            "peak_min": plo, "peak_max": phi}

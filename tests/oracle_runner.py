@@ -15,11 +15,8 @@ SRC = os.path.join(ROOT, "oracle", "inet_oracle.cpp")
 BIN = os.path.join(ROOT, "oracle", "inet_oracle")
 
 
-def compile_oracle(out: str, defines: dict | None = None) -> str:
-    cmd = ["g++", "-O2", "-std=c++17", "-pthread", SRC, "-o", out]
-    for k, v in (defines or {}).items():
-        cmd.insert(1, f"-D{k}={v}")
-    subprocess.run(cmd, check=True)
+def compile_oracle(out: str, src: str = SRC) -> str:
+    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", src, "-o", out], check=True)
     return out
 
 

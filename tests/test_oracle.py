@@ -197,6 +197,16 @@ def test_rounds_profile_sums_to_interactions(oracle):
     assert r["rounds"] == [1] * 21
 
 
+def test_peak_live_of_addition(oracle):
+    # Add(y, r) = S(x) keeps two agents for two; Add(y, r) = Z removes both:
+    # the most agents alive is what the net starts with, Add and the numerals
+    # S^m Z and S^n Z, in every order: m + n + 3
+    for m, n in ((0, 0), (1, 0), (7, 3), (40, 200)):
+        for mode in ("lifo", "fifo", "rounds"):
+            r = oracle.run(R, W.add_net(m, n), mode=mode)[0]
+            assert r["peak_live"] == m + n + 3 and r["live"] == m + n + 1
+
+
 BRUTE = [W.add_net(2, 1), W.mul_net(1, 2), W.mul_net(2, 2), W.ack_net(1, 1), W.ack_net(2, 1),
          W.fib_net(3), W.fib_net(4), "< a, b | Dup(a, b) = S(S(Z)) >",
          "< r | Add(y, r) = S(Z), Add(S(Z), y) = Z >"]
@@ -212,6 +222,11 @@ def test_bruteforce_all_orders(oracle, net):
     r = oracle.run(R, net)[0]
     assert r["result"] == text and r["residual_eqs"] == residual
     assert r["interactions"] == bf["min"]
+    # the oracle's peak of live agents is that of one reduction path, in
+    # every schedule it offers
+    for mode in ("lifo", "fifo", "random", "rounds"):
+        p = oracle.run(R, net, mode=mode)[0]["peak_live"]
+        assert bf["peak_min"] <= p <= bf["peak_max"], (mode, p, bf["peak_min"], bf["peak_max"])
 
 
 # --- the linker cases of Sec. 3.6 and degenerate nets ---------------------------

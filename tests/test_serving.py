@@ -50,6 +50,9 @@ class FakeEvaluator:
         self.held_max = max(self.held_max, len(self.left))
         return i
 
+    def load_nets(self, texts):
+        return [self.load_net(t) for t in texts]
+
     def free(self, ids):
         for i in ids:
             assert self.left[i] == 0 and i not in (self.batch or [])
