@@ -64,8 +64,15 @@ typedef struct inet_arena_cfg {
                           buffers of 8 bytes per pair plus an 8-byte sequence number
                           per cell of the asynchronous driver's ticket queue */
   uint32_t max_nets;   /* independent nets held at once (default 1<<16) */
-  uint32_t reserved;
+  uint32_t flags;      /* INET_ARENA_* bits (default 0) */
 } inet_arena_cfg;
+
+/* inet_arena_cfg.flags: keep the owning net of every name slot in use (4
+ * bytes per name slot, and one store per name a reduction creates), which
+ * inet_free_nets needs to find a net's names.  Without it inet_free_nets
+ * returns INET_ERR_STATE; a batch that is reduced and read back once has no
+ * use for it. */
+#define INET_ARENA_FREE_NETS 1u
 
 /* How the step loop of Sec. 3.6 (evaluate()) is driven. */
 enum {
@@ -283,7 +290,8 @@ inet_status inet_readback_nats_end(inet_ctx* ctx, int32_t wait, uint64_t* values
  * later loads.  Nets are independent configurations (Sec. 2.2,
  * Configurations): nothing outside a net can reach its agents or names, so
  * once its result has been read back (->col / ->sub, Theorem 1) it can go.
- * Every listed net must have been staged or reduced and must have no active
+ * The context must have been created with INET_ARENA_FREE_NETS (else
+ * INET_ERR_STATE).  Every listed net must have been staged or reduced and must have no active
  * pair left (normal form, or stopped by INET_ERR_NO_RULE); otherwise
  * INET_ERR_STATE and nothing is freed.  A net listed twice is
  * INET_ERR_INVALID_ARG; a net in the non-blocking readback in flight is
@@ -339,6 +347,25 @@ inet_status inet_reset(inet_ctx* ctx);
  * interaction rate beside the HBM roofline. */
 inet_status inet_bench_exch(int device, uint64_t n_slots, uint64_t n_ops, double* exch_per_s_out);
 
+/* Microbenchmark of the latency floor of a chain of interactions: one
+ * thread follows a random cycle through an array of n_slots 16-byte records
+ * (allocated and freed here; 16 MB at 2^20 slots stays in L2) for `hops`
+ * dependent steps, each step one of
+ *   variant 0: the load of the next record (a chain of interactions whose
+ *              next pair is known from the record just read, as Add(y, r) =
+ *              S(x) meets the S agent x next);
+ *   variant 1: an atomic exchange whose result names the next record, then
+ *              that record's load (->com finding an agent waiting in a name
+ *              slot, Sec. 2.2);
+ *   variant 2: a record store, a fence, the exchange and the load (one level
+ *              of a chain of second arrivals: the new agent, its publication,
+ *              ->com, and the found agent's record).
+ * *ns_per_hop_out gets nanoseconds per step.  hops <= n_slots - 1 (the
+ * exchange variants consume one slot per step).  The paper has no
+ * counterpart: it gives the hardware floor that the measured time per level
+ * of a batch is compared with. */
+inet_status inet_bench_chase(int device, uint64_t n_slots, uint64_t hops, int32_t variant, double* ns_per_hop_out);
+
 /* ---- Control: the paper's communication phase ------------------------------
  * Sec. 3.5 resolves ->com by sorting every name-headed equation x = t by the
  * name and folding adjacent equations x = t, x = s into s = t (reduce_by_key),
@@ -386,11 +413,20 @@ inet_status inet_control_segsum(int device, const int32_t* in, uint64_t n, int32
  *     step, at most 4096 nets in the context.  Larger sizes are rejected
  *     with INET_ERR_INVALID_ARG before any device work.
  *   - The first call on a device looks the array's address up on that
- *     device (cudaGetSymbolAddress); make that first call before any stream
- *     capture begins.
+ *     device (cudaGetSymbolAddress) and keeps it for the process; make that
+ *     first call before any stream capture begins, and do not reset the
+ *     device (cudaDeviceReset) between calls, which would leave the kept
+ *     address stale.
  *   - All calls on a device share the array, and each call clears what must
  *     start at zero.  Calls that overlap on the GPU race: issue them one at
  *     a time (the call returns only after its device work is finished).
+ *   - The numeral is read back by one device thread walking it (there is
+ *     no room in the fixed array for the list ranking of
+ *     inet_readback_nats): one dependent load per S agent and name slot on
+ *     its path, about a microsecond each, so a numeral of a million
+ *     elements costs about a second.
+ *   - The context's nets must have been staged from slot 0 (every load of
+ *     a host-only context is); otherwise INET_ERR_STATE.
  * On success *value_out is k when the net's interface is the numeral S^k(Z)
  * (otherwise INET_ERR_INVALID_ARG) and *interactions_out (may be NULL) the
  * number of interactions. */

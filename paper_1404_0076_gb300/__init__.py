@@ -49,12 +49,15 @@ class Evaluator:
     and loading without a GPU).
 
     The workspace is one uint8 tensor from PyTorch's caching allocator and
-    the context runs on PyTorch's current stream of that device."""
+    the context runs on PyTorch's current stream of that device.
+    free_nets=True keeps the owner of every name slot, so that finished nets
+    can be freed (free()); it costs one store per name a reduction creates."""
 
     def __init__(self, device: int = 0, max_agents: int = 0, max_vars: int = 0, max_pairs: int = 0,
-                 max_nets: int = 0, use_torch: bool = True):
+                 max_nets: int = 0, use_torch: bool = True, free_nets: bool = False):
         from . import capi
-        self.cfg = capi.inet_arena_cfg(max_agents, max_vars, max_pairs, max_nets, 0)
+        self.cfg = capi.inet_arena_cfg(max_agents, max_vars, max_pairs, max_nets,
+                                       capi.INET_ARENA_FREE_NETS if free_nets else 0)
         self.device = device
         self._ws = None
         stream = None

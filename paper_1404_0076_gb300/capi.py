@@ -37,6 +37,7 @@ INET_MODE_PERSISTENT = 2
 INET_MODE_ASYNC = 3
 INET_MODE_PAPER = 4
 INET_MAX_RULES = 64
+INET_ARENA_FREE_NETS = 1
 
 EXPORTED = [
     "inet_workspace_bytes", "inet_create", "inet_attach_workspace", "inet_destroy",
@@ -45,7 +46,7 @@ EXPORTED = [
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
     "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
-    "inet_free_nets", "inet_free_net", "inet_arena_usage",
+    "inet_free_nets", "inet_free_net", "inet_arena_usage", "inet_bench_chase",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -53,7 +54,7 @@ READ_CHUNK = 65536  # nets per non-blocking readback batch
 
 class inet_arena_cfg(C.Structure):
     _fields_ = [("max_agents", C.c_uint64), ("max_vars", C.c_uint64), ("max_pairs", C.c_uint64),
-                ("max_nets", C.c_uint32), ("reserved", C.c_uint32)]
+                ("max_nets", C.c_uint32), ("flags", C.c_uint32)]
 
 
 class inet_reduce_opts(C.Structure):
@@ -124,6 +125,7 @@ def _load():
                                 C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback_nats_begin": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_bench_exch": ([C.c_int, C.c_uint64, C.c_uint64, C.POINTER(C.c_double)], C.c_int32),
+        "inet_bench_chase": ([C.c_int, C.c_uint64, C.c_uint64, C.c_int32, C.POINTER(C.c_double)], C.c_int32),
         "inet_control_link": ([C.c_int, C.POINTER(C.c_uint64), C.c_uint64, C.c_uint32, C.c_int32,
                                C.POINTER(C.c_uint32), C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
                                C.POINTER(C.c_double)], C.c_int32),
@@ -318,6 +320,12 @@ def inet_bench_exch(device: int, n_slots: int, n_ops: int) -> float:
     if st != INET_OK:
         raise InetError(st, "inet_bench_exch failed")
     return out.value
+
+
+def inet_bench_chase(device: int, n_slots: int, hops: int, variant: int) -> float:
+    ns = C.c_double()
+    _check(None, LIB.inet_bench_chase(device, n_slots, hops, variant, C.byref(ns)))
+    return ns.value
 
 
 def inet_control_link(device: int, eq, n_vars: int, method: int):

@@ -58,7 +58,7 @@ inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
 
 bool valid_cfg(const inet_arena_cfg& c) {
   return c.max_agents <= kMaxIndex + 1ull && c.max_vars <= kMaxIndex + 1ull && c.max_pairs <= 0xFFFFFFFFull &&
-         c.max_nets <= kMaxNetSlots;
+         c.max_nets <= kMaxNetSlots && (c.flags & ~INET_ARENA_FREE_NETS) == 0;
 }
 
 Layout layout_of(const inet_arena_cfg& c) {
@@ -68,7 +68,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.ctrl = take(sizeof(Ctrl));
   L.node = take(sizeof(Node) * c.max_agents);
   L.var = take(sizeof(uint32_t) * c.max_vars);
-  L.vown = take(sizeof(uint32_t) * c.max_vars);
+  L.vown = take((c.flags & INET_ARENA_FREE_NETS) ? sizeof(uint32_t) * c.max_vars : 0);
   L.front0 = take(sizeof(Pair) * c.max_pairs);
   L.front1 = take(sizeof(Pair) * c.max_pairs);
   L.qseq = take(sizeof(unsigned long long) * c.max_pairs);
@@ -193,6 +193,40 @@ struct DeviceGuard {
   }
 };
 
+// Raises the dynamic shared-memory limit of a kernel on the current device
+// to at least `bytes` and never lowers it: the attribute belongs to the
+// kernel for the whole process, so lowering it for one context could make a
+// concurrent launch of another context, which needs more, fail.  A fixed
+// table (no allocation): kernel k on device d.
+enum { kSmemStep = 0, kSmemPersistent = 2, kSmemAsync = 4, kSmemKernels = 6 };  // + 1: owners kept
+std::mutex g_smem_mu;
+size_t g_smem_set[kSmemKernels][256] = {};
+
+cudaError_t raise_smem(int which, const void* func, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  size_t& cur = g_smem_set[which][dev];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
+// The loop kernels a context launches: the instantiations that keep name
+// owners and free marks when it was created with INET_ARENA_FREE_NETS.
+using KernelFn = void (*)(Dev);
+struct LoopKernels {
+  KernelFn step, persistent, async;
+  int track;
+};
+LoopKernels loop_kernels(bool track) {
+  if (track) return {k_step<true>, k_persistent<true>, k_async<true>, 1};
+  return {k_step<false>, k_persistent<false>, k_async<false>, 0};
+}
+
 inet_status fail(inet_ctx* c, inet_status code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -231,7 +265,7 @@ void fill_dev(inet_ctx* ctx) {
   d.qseq = at<unsigned long long>(ctx, L.qseq);
   d.afree = at<uint32_t>(ctx, L.afree);
   d.vfree = at<uint32_t>(ctx, L.vfree);
-  d.vown = at<uint32_t>(ctx, L.vown);
+  d.vown = (ctx->cfg.flags & INET_ARENA_FREE_NETS) ? at<uint32_t>(ctx, L.vown) : nullptr;
   d.netctr = at<unsigned long long>(ctx, L.netctr);
   d.netstat = at<int32_t>(ctx, L.netstat);
   d.netrep = at<uint32_t>(ctx, L.netrep);
@@ -330,7 +364,7 @@ inet_status upload_staged(inet_ctx* ctx) {
   if (ta) CK(h2d(ctx, ctx->dev.node + a0, ctx->st_nodes.data(), (size_t)ta * sizeof(Node)));
   if (tv) {
     CK(h2d(ctx, ctx->dev.var + v0, ctx->st_vars.data(), (size_t)tv * sizeof(uint32_t)));
-    CK(h2d(ctx, ctx->dev.vown + v0, ctx->st_vown.data(), (size_t)tv * sizeof(uint32_t)));
+    if (ctx->dev.vown) CK(h2d(ctx, ctx->dev.vown + v0, ctx->st_vown.data(), (size_t)tv * sizeof(uint32_t)));
   }
   const size_t nn = ctx->st_netctr.size();
   if (nn) {
@@ -517,7 +551,7 @@ inet_status build_graph(inet_ctx* ctx, int block, int grid, size_t smem) {
   void* args[] = {&d};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = (void*)k_step;
+  kp.func = (void*)loop_kernels(ctx->dev.vown != nullptr).step;
   kp.gridDim = dim3((unsigned)grid);
   kp.blockDim = dim3((unsigned)block);
   kp.sharedMemBytes = (unsigned)smem;
@@ -993,16 +1027,17 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   const size_t smem = smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl, 0);
   const size_t smem_p = smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl, d.solo_max);
   if (smem_p > kMaxSmem) return fail(ctx, INET_ERR_INVALID_ARG, "block size and solo_max need too much shared memory");
-  CK(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CK(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+  const LoopKernels K = loop_kernels(d.vown != nullptr);
+  CK(raise_smem(kSmemStep + K.track, (const void*)K.step, smem));
+  CK(raise_smem(kSmemPersistent + K.track, (const void*)K.persistent, smem_p));
   CK(cudaEventRecord(ctx->ev0, ctx->stream));
   uint64_t launches = 0;
   bool async_paused = false;
   if (fc[cur] > 0 && o.mode == INET_MODE_ASYNC) {
     const size_t smem_a = async_smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl);
-    CK(cudaFuncSetAttribute(k_async, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+    CK(raise_smem(kSmemAsync + K.track, (const void*)K.async, smem_a));
     int per = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async, B, smem_a));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K.async, B, smem_a));
     const int maxg = std::max(1, per) * ctx->num_sms;
     // default: one block per SM (more warps mostly add idle polling)
     const int grid = o.grid > 0 ? std::min(o.grid, maxg) : maxg;
@@ -1015,7 +1050,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
       k_async_fill<<<fill_blocks, 256, 0, ctx->stream>>>(d);
       k_async_prep<<<1, 1, 0, ctx->stream>>>(d);
       void* args[] = {&d};
-      CK(cudaLaunchCooperativeKernel((const void*)k_async, dim3((unsigned)grid), dim3((unsigned)B), args, smem_a,
+      CK(cudaLaunchCooperativeKernel((const void*)K.async, dim3((unsigned)grid), dim3((unsigned)B), args, smem_a,
                                      ctx->stream));
       k_async_post<<<1, 1, 0, ctx->stream>>>(d);
       CK(cudaGetLastError());
@@ -1070,7 +1105,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
       if (pending) {
         k_paper_prep<<<1, 1, 0, ctx->stream>>>(dp);
         const uint32_t grid = std::max<uint32_t>(1, (pending + (uint32_t)B - 1) / (uint32_t)B);
-        k_step<<<grid, B, smem, ctx->stream>>>(dp);
+        K.step<<<grid, B, smem, ctx->stream>>>(dp);
         // the dummies out, the equations after those already in the array
         const uint64_t mf = (uint64_t)pending * nfix;
         const uint32_t ft = (uint32_t)((mf + kCpTile - 1) / kCpTile);
@@ -1128,7 +1163,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
       uint32_t pending = fc[cur];
       for (;;) {
         const uint32_t grid = std::max<uint32_t>(1, (pending + (uint32_t)B - 1) / (uint32_t)B);
-        k_step<<<grid, B, smem, ctx->stream>>>(d);
+        K.step<<<grid, B, smem, ctx->stream>>>(d);
         CK(cudaGetLastError());
         launches++;
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -1148,14 +1183,14 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
       if (o.mode == INET_MODE_GRAPH) {
         if (grid <= 0) {
           int per = 0;
-          CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step, B, smem));
+          CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K.step, B, smem));
           grid = std::max(1, per) * ctx->num_sms;
         }
         s = build_graph(ctx, B, grid, smem);
         if (s) return s;
       } else {
         int per = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem_p));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K.persistent, B, smem_p));
         const int maxg = std::max(1, per) * ctx->num_sms;
         grid = grid > 0 ? std::min(grid, maxg) : maxg;
         // the step word the blocks start from
@@ -1169,7 +1204,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
           CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
         } else {
           void* args[] = {&d};
-          CK(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3((unsigned)B), args,
+          CK(cudaLaunchCooperativeKernel((const void*)K.persistent, dim3((unsigned)grid), dim3((unsigned)B), args,
                                          smem_p, ctx->stream));
         }
         launches++;
@@ -1474,6 +1509,8 @@ inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
   if (!ctx || n < 0 || (uint32_t)n > kReadChunk || (n > 0 && !net_ids)) return INET_ERR_INVALID_ARG;
   if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
   if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  if (!(ctx->cfg.flags & INET_ARENA_FREE_NETS))
+    return fail(ctx, INET_ERR_STATE, "the context keeps no name owners: create it with INET_ARENA_FREE_NETS");
   if (n == 0) return INET_OK;
   std::vector<uint8_t> listed(ctx->nets.size(), 0);
   for (int32_t i = 0; i < n; i++) {
@@ -1661,6 +1698,63 @@ inet_status inet_bench_exch(int device, uint64_t n_slots, uint64_t n_ops, double
   return st;
 }
 
+inet_status inet_bench_chase(int device, uint64_t n_slots, uint64_t hops, int32_t variant, double* ns_per_hop_out) {
+  if (!ns_per_hop_out || n_slots < 2 || n_slots > (1ull << 28) || hops == 0 || hops > n_slots - 1 || variant < 0 ||
+      variant > 2)
+    return INET_ERR_INVALID_ARG;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return INET_ERR_NO_DEVICE;
+  DeviceGuard g(device);
+  // a random cyclic permutation (Sattolo's algorithm; splitmix64 stream)
+  std::vector<uint32_t> nxt(n_slots);
+  for (uint64_t i = 0; i < n_slots; i++) nxt[i] = (uint32_t)i;
+  uint64_t st64 = 0x1404007614040076ull;
+  for (uint64_t i = n_slots - 1; i > 0; i--) {
+    uint64_t z = (st64 += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const uint64_t j = z % i;  // j < i
+    std::swap(nxt[i], nxt[j]);
+  }
+  std::vector<int4> hrec(n_slots);
+  for (uint64_t i = 0; i < n_slots; i++) hrec[i] = make_int4((int)nxt[i], 0, 0, 0);
+  int4 *rec = nullptr, *wrk = nullptr;
+  uint32_t* xs = nullptr;
+  unsigned long long* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  inet_status st = INET_OK;
+  float ms = 0;
+  const uint32_t warm = (uint32_t)std::min<uint64_t>(hops, 1024);
+  if (cudaMalloc(&rec, n_slots * sizeof(int4)) != cudaSuccess || cudaMalloc(&wrk, n_slots * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&xs, n_slots * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&sink, 8) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = INET_ERR_CUDA;
+  } else if (cudaMemcpy(rec, hrec.data(), n_slots * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(xs, nxt.data(), n_slots * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    st = INET_ERR_CUDA;
+  } else {
+    // the timed chase starts where a short warm-up one ended, so both stay
+    // within one lap of the cycle (hops + warm-up <= n_slots - 1 is checked
+    // for the exchange variants by the caller's sizes; the load variant may
+    // lap)
+    k_bench_chase<<<1, 32>>>(rec, xs, wrk, 0u, warm, 0, sink);
+    cudaEventRecord(e0);
+    k_bench_chase<<<1, 32>>>(rec, xs, wrk, 0u, (uint32_t)hops, variant, sink);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = INET_ERR_CUDA;
+    else cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (st == INET_OK) *ns_per_hop_out = 1e6 * (double)ms / (double)hops;
+  if (rec) cudaFree(rec);
+  if (wrk) cudaFree(wrk);
+  if (xs) cudaFree(xs);
+  if (sink) cudaFree(sink);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
+}
+
 inet_status inet_control_link(int device, const uint64_t* eq, uint64_t n, uint32_t n_vars, int32_t method,
                               uint32_t* pairs_out, uint64_t cap, uint64_t* n_pairs_out, uint32_t* passes_out,
                               double* ms_out) {
@@ -1830,7 +1924,9 @@ std::mutex g_fixed_mu;
 void* g_fixed_addr[256] = {};
 
 // Device address of the fixed scratch on `device`, looked up once per device
-// with that device current.
+// with that device current.  The address stays valid while the device's
+// primary context lives: a device reset (cudaDeviceReset) between calls
+// would leave it stale, which the header rules out.
 inet_status fixed_scratch(int device, void** out) {
   std::lock_guard<std::mutex> lock(g_fixed_mu);
   if (device < 0 || device >= 256) return INET_ERR_INVALID_ARG;
@@ -1894,6 +1990,10 @@ extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void
     return fail(ctx, INET_ERR_INVALID_ARG, "net has more initial active pairs than the fixed frontier holds");
   if (ctx->st_nodes.size() > max_agents || ctx->st_vars.size() > max_vars)
     return fail(ctx, INET_ERR_INVALID_ARG, "the context's nets do not fit max_agents / max_vars");
+  // the staged nets are copied to arena offset 0 with the net's own pairs
+  // as they are: that holds only while staging started at slot 0
+  if (ctx->st_a0 != 0 || ctx->st_v0 != 0 || ctx->st_nodes.size() != ctx->a_bump || ctx->st_vars.size() != ctx->v_bump)
+    return fail(ctx, INET_ERR_STATE, "the host-only context's staged nets do not start at slot 0");
   if (arena_bytes < var_off + sizeof(uint32_t) * max_vars || (reinterpret_cast<uintptr_t>(arena) & 255))
     return fail(ctx, INET_ERR_INVALID_ARG, "arena smaller than 16*max_agents (rounded to 256) + 4*max_vars, or not 256-byte aligned");
   int ndev = 0;
@@ -1972,15 +2072,15 @@ extern "C" inet_status inet_reduce_into(inet_ctx* host_ctx, int32_t net_id, void
   const size_t smem = smem_bytes(B, d.n_labels, d.n_tmpl, d.solo_max);
   int nsm = 0, per = 0;
   FX(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-  FX(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FX(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent, B, smem));
+  FX(raise_smem(kSmemPersistent, (const void*)k_persistent<false>, smem));
+  FX(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<false>, B, smem));
   const int grid = std::max(1, per) * nsm;
   if (!nr.pairs.empty()) {
     const unsigned long long word0 = pack_word((uint32_t)nr.pairs.size(), 0, 0, 0);
     FX(cudaMemcpyAsync(&d.ctrl->bar_word, &word0, 8, cudaMemcpyHostToDevice, st));
     for (;;) {
       void* args[] = {&d};
-      FX(cudaLaunchCooperativeKernel((const void*)k_persistent, dim3((unsigned)grid), dim3((unsigned)B), args, smem, st));
+      FX(cudaLaunchCooperativeKernel((const void*)k_persistent<false>, dim3((unsigned)grid), dim3((unsigned)B), args, smem, st));
       uint32_t hit = 0;
       FX(cudaMemcpyAsync(&hit, &d.ctrl->hit_slice, 4, cudaMemcpyDeviceToHost, st));
       FX(cudaStreamSynchronize(st));

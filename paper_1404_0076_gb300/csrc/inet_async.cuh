@@ -23,6 +23,13 @@
 // of an agent through an exchange loads its record only after the exchange
 // returned (address dependency), so it sees the record written before the
 // fence.
+//
+// kTrack (contexts created with INET_ARENA_FREE_NETS): the kernel also keeps
+// what inet_free_nets scans for: the owning net of every name it creates,
+// the free mark of every agent slot it frees, and both marks on the unused
+// slots its warps return at the end.  The other instantiation has none of
+// that code in its loop (code the loop does not run still costs this kernel
+// time through instruction fetch and scheduling).
 #pragma once
 
 #include "inet_kernels.cuh"
@@ -76,6 +83,7 @@ __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned lon
 // new records before linking; a lane that receives a reference through an
 // exchange loads the referenced record only after the exchange returned
 // (address dependency), so it sees the record written before the fence.
+template <bool kTrack>
 __device__ __forceinline__ bool link_async(const Dev& d, WarpMem& W, uint32_t t, uint32_t u, Pair* out) {
   for (uint32_t guard = 0;; guard++) {
     if (is_agent(t) && is_agent(u)) {
@@ -96,7 +104,7 @@ __device__ __forceinline__ bool link_async(const Dev& d, WarpMem& W, uint32_t t,
     const uint32_t old = atomicExch(d.var + x, u);
     if (old == kEmpty) return false;
     __stcg(d.var + x, kEmpty);
-    if (d.vown) __stcg(d.vown + x, kNoNet);
+    if constexpr (kTrack) __stcg(d.vown + x, kNoNet);
     const int pos = atomicAdd(&W.vstage_n, 1);
     if (pos < kVStageW) {
       W.vstage[pos] = x;
@@ -145,6 +153,7 @@ struct WarpStacks {
 // active pairs are left in W.out[0..return)[lane]; a pair that cannot be
 // reduced (no rule, corrupt state) is dropped and returns 0.  Lane 0's
 // `live` collects the change of live agents.
+template <bool kTrack>
 __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl* tmpl, const int16_t* tab,
                                                    uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
                                                    uint32_t a, uint32_t b, long long& live, bool pre,
@@ -248,7 +257,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
         in_range = false;
       } else {
         __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's fence
-        if (d.vown) __stcg(d.vown + x, net);
+        if constexpr (kTrack) __stcg(d.vown + x, net);
       }
       W.vals[kValFresh + v][lane] = mk_var(x);
     }
@@ -275,7 +284,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
       for (uint32_t f = 0; f < free_a; f++) {
         const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
         const uint32_t k = of + f;
-        __stcg(&d.node[slot].head, kFreeHead);
+        if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
         if (k < keep) W.astk[atop + k] = slot;
         else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
       }
@@ -338,7 +347,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
           // second arrival: the slot is finished; continue with old = u
           const uint32_t x = idx_of(t);
           __stcg(d.var + x, kEmpty);
-          if (d.vown) __stcg(d.vown + x, kNoNet);
+          if constexpr (kTrack) __stcg(d.vown + x, kNoNet);
           const int pos = atomicAdd(&W.vstage_n, 1);
           if (pos < kVStageW) {
             W.vstage[pos] = x;
@@ -347,7 +356,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
             __stcg(d.vfree + tp % d.cap_vars, x);
           }
           Pair out;
-          if (link_async(d, W, lo[k], u, &out)) {
+          if (link_async<kTrack>(d, W, lo[k], u, &out)) {
             W.out[np][lane] = out;
             np++;
           }
@@ -357,7 +366,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
     for (uint32_t k = kBatch; k < nl; k++) {
       const uint32_t lk = T.link[k];
       Pair out;
-      if (link_async(d, W, W.vals[lk & 0xFFu][lane], W.vals[lk >> 8][lane], &out)) {
+      if (link_async<kTrack>(d, W, W.vals[lk & 0xFFu][lane], W.vals[lk >> 8][lane], &out)) {
         W.out[np][lane] = out;
         np++;
       }
@@ -438,6 +447,7 @@ __device__ __forceinline__ bool wait_ticket(const Dev& d, const Pair* Q, unsigne
   }
 }
 
+template <bool kTrack>
 __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t off = 0;
@@ -553,7 +563,7 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
       continue;
     }
     nap = 0;
-    const uint32_t np = async_interact(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb);
+    const uint32_t np = async_interact<kTrack>(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb);
     // keep the first new pair and start loading its records now, so the
     // load overlaps the rest of this iteration
     const bool had = have;
@@ -733,9 +743,9 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
       }
     }
   }
-  // free slots known only to this warp go back to the rings, marked free:
-  // a stack also holds slots fetched from the pools and never used, which
-  // may come fresh from the bump pointer with stale contents
+  // free slots known only to this warp go back to the rings (when owners are
+  // kept, marked free: a stack also holds slots fetched from the pools and
+  // never used, which may come from the bump pointer with stale contents)
   __syncwarp();
   {
     unsigned long long ab = 0, vb = 0;
@@ -747,12 +757,16 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
     vb = __shfl_sync(kFull, vb, 0);
     for (int j = lane; j < S.ac; j += 32) {
       const uint32_t sl = W.astk[j];
-      if (sl < d.cap_agents) __stcg(&d.node[sl].head, kFreeHead);
+      if constexpr (kTrack) {
+        if (sl < d.cap_agents) __stcg(&d.node[sl].head, kFreeHead);
+      }
       __stcg(d.afree + (ab + j) % d.cap_agents, sl);
     }
     for (int j = lane; j < S.vc; j += 32) {
       const uint32_t x = W.vstk[j];
-      if (d.vown && x < d.cap_vars) __stcg(d.vown + x, kNoNet);
+      if constexpr (kTrack) {
+        if (x < d.cap_vars) __stcg(d.vown + x, kNoNet);
+      }
       __stcg(d.vfree + (vb + j) % d.cap_vars, x);
     }
   }

@@ -188,16 +188,15 @@ __global__ void k_place(Dev d, uint32_t a0, uint32_t ta, uint32_t v0, uint32_t t
     if (j < tv) {
       const uint32_t src = v0 + j;
       const uint32_t w = tr(__ldcg(d.var + src));
-      const uint32_t o = __ldcg(d.vown + src);
       const uint32_t dst = src >= vmov ? taken_slot(d.vfree, d.cap_vars, vh, src - vmov) : src;
       if (dst >= v0 && dst != src) {
         set_error(d.ctrl, INET_ERR_STATE, 32);
       } else {
         __stcg(d.var + dst, w);
-        __stcg(d.vown + dst, o);
+        if (d.vown) __stcg(d.vown + dst, __ldcg(d.vown + src));
         if (dst != src) {
           __stcg(d.var + src, kEmpty);
-          __stcg(d.vown + src, kNoNet);
+          if (d.vown) __stcg(d.vown + src, kNoNet);
         }
       }
     }

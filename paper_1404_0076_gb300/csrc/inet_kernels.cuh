@@ -85,7 +85,7 @@ struct Dev {
   unsigned long long* qseq;  // asynchronous kernel: sequence number of each ticket queue cell
   uint32_t* afree;
   uint32_t* vfree;
-  uint32_t* vown;        // net owning each name slot in use (kNoNet when free); NULL: not kept
+  uint32_t* vown;        // net owning each name slot in use (kNoNet when free); NULL: owners not kept
   unsigned long long* netctr;
   int32_t* netstat;
   uint32_t* netrep;      // 1 once inet_net_finished reported the net
@@ -350,6 +350,7 @@ __device__ __forceinline__ uint32_t pool_slot(const uint32_t* ring, unsigned lon
 // which resolves chains x1 = x2 = .. of any length in one call (the chains of
 // Sec. 3.6 that need several passes of the sorting algorithm).  Returns true
 // and the pair when an active pair results.
+template <bool kTrack>
 __device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t, uint32_t u, Pair* out,
                                         unsigned long long slot) {
   for (uint32_t guard = 0;; guard++) {
@@ -379,7 +380,7 @@ __device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t,
     if (old == kEmpty) return false;
     // second arrival: the slot is finished; clear it and free it
     __stcg(d.var + x, kEmpty);
-    if (d.vown) __stcg(d.vown + x, kNoNet);
+    if constexpr (kTrack) __stcg(d.vown + x, kNoNet);
     const int pos = atomicAdd(&s.misc[M_NVSTAGE], 1);
     if (pos < kVarStage * (int)blockDim.x) {
       s.vstage[pos] = x;
@@ -394,7 +395,10 @@ __device__ __forceinline__ bool link_eq(const Dev& d, const Smem& s, uint32_t t,
 // One chunk of the frontier: pairs [base, base + blockDim.x) of frontier
 // `cur` (n pairs), read from global memory or, for SOLO, from the block's
 // shared solo frontier.  All threads of the block call it together.
-template <bool SOLO>
+// kTrack (contexts created with INET_ARENA_FREE_NETS): the owning net of
+// every fresh name and the free mark of every agent slot freed are kept for
+// inet_free_nets; the other instantiation carries none of that code.
+template <bool SOLO, bool kTrack>
 __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32_t n, uint32_t cur) {
   const uint32_t tid = threadIdx.x, B = blockDim.x;
   const int lane = tid & 31;
@@ -538,7 +542,7 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
         if (k < tv) x = s.lv[lv0 + k];
         else x = pool_slot(d.vfree, d.cap_vars, s.warp[W_VRING], (uint32_t)s.warp[W_VAVAIL], s.warp[W_VBUMP], k - tv);
         if (x >= d.cap_vars) in_range = false;
-        else if (d.vown) __stcg(d.vown + x, net);
+        else if constexpr (kTrack) __stcg(d.vown + x, net);  // the owner, before the name is published
         vals[(kValFresh + v) * B] = mk_var(x);
       }
     }
@@ -577,7 +581,7 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
   for (uint32_t k = 0; k < max_link; k++) {
     Pair out;
     bool has = false;
-    if (k < n_link) has = link_eq(d, s, vals[T.link[k][0] * B], vals[T.link[k][1] * B], &out, slot0 + k);
+    if (k < n_link) has = link_eq<kTrack>(d, s, vals[T.link[k][0] * B], vals[T.link[k][1] * B], &out, slot0 + k);
     const unsigned m = __ballot_sync(kFull, has);
     if (m) {
       const int leader = __ffs(m) - 1;
@@ -647,7 +651,7 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
       for (uint32_t f = 0; f < free_a; f++) {
         const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
         const uint32_t k = of + f;
-        __stcg(&d.node[slot].head, kFreeHead);
+        if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
         if (k < keep) s.la[base0 + k] = slot;
         else __stcg(d.afree + (s.warp[W_AFREE] + (k - keep)) % d.cap_agents, slot);
       }
@@ -734,6 +738,7 @@ __device__ void finalize_step(const Dev& d) {
 
 // One step of the loop; the last block to finish runs finalize_step().
 // Used by the plain host loop and by the CUDA-graph loop.
+template <bool kTrack>
 __global__ void __launch_bounds__(512) k_step(Dev d) {
   Smem s = carve(d, 0);
   load_tables(d, s);
@@ -744,7 +749,7 @@ __global__ void __launch_bounds__(512) k_step(Dev d) {
   const bool stop = ld_volatile(&c->done) != 0;
   if (!stop) {
     for (uint32_t chunk = blockIdx.x; (unsigned long long)chunk * blockDim.x < n; chunk += gridDim.x)
-      process_chunk<false>(d, s, chunk * blockDim.x, n, cur);
+      process_chunk<false, kTrack>(d, s, chunk * blockDim.x, n, cur);
   }
   spill_local(d, s);
   flush_live(d, s);
@@ -875,6 +880,7 @@ __device__ bool bounded_wait(const Dev& d, Pred pred, uint32_t nap_max) {
 // Block 0 alone: steps with the frontier in shared memory, until it is
 // empty, grows beyond solo_max, or the call must stop; then the frontier
 // goes back to global memory and the step word is published.
+template <bool kTrack>
 __device__ void solo_phase(const Dev& d, const Smem& s, uint32_t n, uint32_t gcur) {
   Ctrl* c = d.ctrl;
   const uint32_t tid = threadIdx.x, B = blockDim.x;
@@ -891,7 +897,7 @@ __device__ void solo_phase(const Dev& d, const Smem& s, uint32_t n, uint32_t gcu
   bool done = false;
   for (uint32_t it = 0;; it++) {
     const int32_t fatal_seen = (it & 15) == 15 ? (int32_t)ld_volatile((const uint32_t*)&c->fatal) : 0;
-    for (uint32_t base = 0; base < n; base += B) process_chunk<true>(d, s, base, n, lc);
+    for (uint32_t base = 0; base < n; base += B) process_chunk<true, kTrack>(d, s, base, n, lc);
     if (tid == 0) {
       const uint32_t n_next = (uint32_t)s.misc[M_SFN];
       s.misc[M_SFN] = 0;
@@ -926,6 +932,7 @@ __device__ void solo_phase(const Dev& d, const Smem& s, uint32_t n, uint32_t gcu
   __syncthreads();
 }
 
+template <bool kTrack>
 __global__ void __launch_bounds__(512) k_persistent(Dev d) {
   Smem s = carve(d, d.solo_max);
   load_tables(d, s);
@@ -958,9 +965,9 @@ __global__ void __launch_bounds__(512) k_persistent(Dev d) {
     const uint32_t A = solo ? 1u : min(gridDim.x, nchunks);
     if (coord) {
       if (solo) {
-        solo_phase(d, s, n, cur);
+        solo_phase<kTrack>(d, s, n, cur);
       } else {
-        for (uint32_t ch = 0; ch < nchunks; ch += A) process_chunk<false>(d, s, ch * B, n, cur);
+        for (uint32_t ch = 0; ch < nchunks; ch += A) process_chunk<false, kTrack>(d, s, ch * B, n, cur);
         flush_live(d, s);
         if (tid == 0 && A > 1) {
           if (!bounded_wait(d, [&] { return ld_volatile(&c->bar_count) >= A - 1; }, 64)) s.misc[M_TIMEOUT] = 1;
@@ -982,7 +989,7 @@ __global__ void __launch_bounds__(512) k_persistent(Dev d) {
       }
     } else {
       if (!solo && blockIdx.x < A) {
-        for (uint32_t ch = blockIdx.x; ch < nchunks; ch += A) process_chunk<false>(d, s, ch * B, n, cur);
+        for (uint32_t ch = blockIdx.x; ch < nchunks; ch += A) process_chunk<false, kTrack>(d, s, ch * B, n, cur);
         flush_live(d, s);
         __syncthreads();
         if (tid == 0) {

@@ -65,7 +65,7 @@ class Server:
 
             def make_evaluator():
                 return Evaluator(device, max_agents=self.max_agents, max_vars=self.max_vars,
-                                 max_pairs=max_pairs, max_nets=max_nets)
+                                 max_pairs=max_pairs, max_nets=max_nets, free_nets=True)
         self.ev = make_evaluator()
         self.ev.load_rules(rules)
         self.max_nets = max_nets

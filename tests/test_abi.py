@@ -34,6 +34,15 @@ def test_every_declared_symbol_is_exported(capi):
     assert sorted(capi.EXPORTED) == names
 
 
+def test_owner_tracking_is_a_flag(capi):
+    base = capi.inet_arena_cfg(1 << 16, 1 << 16, 1 << 10, 64, 0)
+    kept = capi.inet_arena_cfg(1 << 16, 1 << 16, 1 << 10, 64, capi.INET_ARENA_FREE_NETS)
+    # 4 bytes per name slot for the owners (256-byte rounding aside)
+    assert capi.inet_workspace_bytes(kept) - capi.inet_workspace_bytes(base) >= 4 * (1 << 16)
+    with pytest.raises(capi.InetError):
+        capi.inet_workspace_bytes(capi.inet_arena_cfg(1 << 16, 1 << 16, 1 << 10, 64, 2))
+
+
 def test_workspace_size_grows_with_capacity(capi):
     small = capi.inet_workspace_bytes(capi.inet_arena_cfg(1000, 1000, 1000, 10, 0))
     big = capi.inet_workspace_bytes(capi.inet_arena_cfg(10 ** 6, 10 ** 6, 10 ** 5, 1000, 0))
@@ -246,6 +255,10 @@ def test_argument_errors_are_reported_not_crashed(capi):
     assert L.inet_arena_usage(ctx, None) == capi.INET_ERR_INVALID_ARG
     assert L.inet_control_link(0, None, 0, 0, 7, None, 0, out, None, None) == capi.INET_ERR_INVALID_ARG
     assert L.inet_bench_exch(0, 0, 0, None) == capi.INET_ERR_INVALID_ARG
+    ns = C.c_double()
+    assert L.inet_bench_chase(0, 1 << 10, 1 << 10, 0, C.byref(ns)) == capi.INET_ERR_INVALID_ARG  # hops > n - 1
+    assert L.inet_bench_chase(0, 1 << 10, 100, 3, C.byref(ns)) == capi.INET_ERR_INVALID_ARG
+    assert L.inet_bench_chase(0, 1 << 10, 100, 0, None) == capi.INET_ERR_INVALID_ARG
 
 
 def test_arena_usage_counts_loaded_nets(capi):

@@ -30,7 +30,7 @@ def make_ev(**kw):
     import torch
     assert torch.cuda.is_available(), "GPU tests need a GPU"
     from paper_1404_0076_gb300 import Evaluator
-    return Evaluator(device=0, **kw)
+    return Evaluator(device=0, free_nets=True, **kw)
 
 
 def check_against(ev, ids, expect, text=True):
@@ -175,6 +175,18 @@ def test_free_errors_leave_everything_in_place(orc):
     assert ev.readback(c) == exp[2]["result"]
     assert ev.readback(d) == exp[0]["result"] and ev.readback(f) == exp[1]["result"]
     ev.close()
+
+
+def test_free_needs_owner_tracking(orc):
+    from paper_1404_0076_gb300 import Evaluator, InetError
+    with Evaluator(device=0, max_agents=1 << 16, max_vars=1 << 16, max_pairs=1 << 12, max_nets=16) as ev:
+        ev.load_rules(R)
+        ids = ev.load_nets([W.add_net(3, 4)])
+        ev.reduce(ids, mode="async")
+        with pytest.raises(InetError) as e:
+            ev.free(ids)
+        assert e.value.name == "STATE"
+        assert ev.readback(ids[0]) == "S(S(S(S(S(S(S(Z)))))))"
 
 
 def test_placement_rewrites_pairs_of_nets_staged_later(orc):
