@@ -496,15 +496,26 @@ def main():
         stc = ev.reduce([], mode="async", block=32, grid=1)
         lone = 1e6 * stc["device_ms"] / max(1, stc["interactions"])
     step_s = total_s / args.steps
+    # the hardware floor of one level: one thread's dependent round trips
+    # through L2 (16 MiB of records), measured here: a record load; an
+    # exchange, then the record it names; a record store, fence, exchange and
+    # load (what a level of second arrivals needs at the least)
+    floor = {name: capi.inet_bench_chase(local, 1 << 20, 1 << 16, v)
+             for v, name in ((0, "load"), (1, "exch_load"), (2, "store_fence_exch_load"))}
+    per_level = floor["store_fence_exch_load"]
     roof["critical_path"] = {"depth_steps": depth,
                              "ns_per_level": 1e9 * step_s / max(1, depth),
+                             "hw_floor_ns": floor,
+                             "bound_ms": depth * per_level * 1e-6,
+                             "frac": depth * per_level * 1e-9 / step_s,
                              "lone_chain_ns_per_interaction": lone,
-                             "bound_ms": depth * lone * 1e-6 if lone else None,
-                             "frac": depth * lone * 1e-9 / step_s if lone else None,
+                             "frac_of_lone_chain": depth * lone * 1e-9 / step_s if lone else None,
                              "how": "depth = steps of the maximally parallel loop (persistent form) on the same batch; "
-                                    "ns_per_level = timed device time per step / depth; lone chain = one warp "
-                                    "reducing Add(Z, r) = S^20000 Z with nothing else running; bound = depth x that "
-                                    "latency, the time if every level of the batch ran at it"}
+                                    "ns_per_level = timed device time per step / depth; bound = depth x the hardware "
+                                    "floor of one level (inet_bench_chase: one thread storing a record, fencing, "
+                                    "exchanging a name slot and loading the record the exchange names, 2^16 dependent "
+                                    "steps over an L2-resident array of 2^20 16-byte records); lone chain = one warp "
+                                    "reducing Add(Z, r) = S^20000 Z with nothing else running, for comparison"}
 
     # e2e: public API from host text to host results, copies included
     e2e_ms, e2e_h2d, e2e_d2h, e2e_int = [], 0, 0, 0
@@ -597,6 +608,8 @@ def main():
     narrow = None
     if rank == 0 and world == 1 and not args.no_narrow:
         narrow = {name: narrow_leg(args, local, name) for name in ("ack3", "fib")}
+        for rec in narrow.values():
+            rec["frac_of_hw_floor"] = per_level / rec["ns_per_level"]
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
