@@ -530,8 +530,8 @@ def main():
             vals, per_net = ev.readback_nats(ids)   # the numerals, walked on the device
             assert all(v is not None for v in vals)
         else:
-            texts = [ev.readback(i) for i in ids]   # the normal forms (->sub / ->col)
-            per_net = [ev.net_info(i)["interactions"] for i in ids]
+            texts = [ev.readback(i) for i in ids]   # the normal forms (->sub / ->col), rendered on the device
+            per_net = [st["interactions"]]          # every net of the batch was reduced by this call
             assert all(texts)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))

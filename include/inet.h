@@ -227,10 +227,22 @@ inet_status inet_transfer_bytes(const inet_ctx* ctx, uint64_t* h2d_out, uint64_t
  * terms left to right, names renamed x0, x1, .. in order of first
  * occurrence, as a NUL-terminated string.  If cap is too small returns
  * INET_ERR_INVALID_ARG with *needed_out set (needed_out may be NULL).  The
- * text is rendered from a host snapshot of the arena, on the pool of host
- * threads, and kept until the arena changes, so a size query followed by
- * the copy renders it once. */
+ * text is rendered on the device: every agent of the net and every port
+ * becomes an element of one list in text order, ranked by pointer jumping
+ * (characters and names after each element), names numbered by first
+ * occurrence, characters written at their offsets; only the text is copied
+ * to the host.  A net whose interface does not unfold into a finite forest
+ * (a subterm reached twice, a cycle) is rendered from a host snapshot of the
+ * arena instead, by a walk with a bound.  The device scratch (48 bytes per
+ * agent slot in use, 4 per name slot) is allocated with cudaMalloc on first
+ * use and grown when needed.  The text is kept until the arena changes, so a
+ * size query followed by the copy renders it once, and inet_net_info of the
+ * same net then takes its live and residual agents from that render. */
 inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, size_t* needed_out);
+
+/* How many texts inet_readback rendered on the device and how many on the
+ * host (either pointer may be NULL).  The paper has no counterpart. */
+inet_status inet_readback_counts(const inet_ctx* ctx, uint64_t* device_out, uint64_t* host_out);
 
 /* If the net's interface is a single numeral S^k(Z), stores k.  Otherwise
  * INET_ERR_INVALID_ARG.  interactions_out (may be NULL) gets the net's

@@ -154,6 +154,10 @@ class Evaluator:
         """Returns the slots and ids of finished nets for reuse (inet_free_nets)."""
         capi_lazy.inet_free_nets(self.ctx, list(net_ids))
 
+    def readback_counts(self) -> tuple[int, int]:
+        """Texts inet_readback rendered on the device and on the host."""
+        return capi_lazy.inet_readback_counts(self.ctx)
+
     def arena_usage(self) -> dict:
         """Bump pointers (agent and name slots handed out) and live agents."""
         return capi_lazy.inet_arena_usage(self.ctx)

@@ -46,7 +46,7 @@ EXPORTED = [
     "inet_trace", "inet_reset", "inet_last_error", "inet_reduce_into", "inet_net_pending",
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
     "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
-    "inet_free_nets", "inet_free_net", "inet_arena_usage", "inet_bench_chase",
+    "inet_free_nets", "inet_free_net", "inet_arena_usage", "inet_bench_chase", "inet_readback_counts",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -112,6 +112,7 @@ def _load():
         "inet_stage": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_nets": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_net": ([P, C.c_int32], C.c_int32),
+        "inet_readback_counts": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_arena_usage": ([P, C.POINTER(inet_arena_usage_t)], C.c_int32),
         "inet_transfer_bytes": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
@@ -243,6 +244,12 @@ def inet_free_nets(ctx, net_ids) -> None:
 
 def inet_free_net(ctx, net_id: int) -> None:
     _check(ctx, LIB.inet_free_net(ctx, net_id))
+
+
+def inet_readback_counts(ctx) -> tuple[int, int]:
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(ctx, LIB.inet_readback_counts(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def inet_arena_usage(ctx) -> dict:

@@ -20,6 +20,7 @@
 #include "inet_free.cuh"
 #include "inet_paper.cuh"
 #include "inet_readback.cuh"
+#include "inet_textdev.cuh"
 #include "inet_text.h"
 
 using namespace inet;
@@ -175,6 +176,21 @@ struct inet_ctx {
   uint2* jump_buf = nullptr;
   uint64_t jump_cap = 0;                    // elements per buffer
   uint32_t* jump_ctl = nullptr;
+  // device text readback: grow-only scratch (inet_textdev.cuh), the label
+  // table of the loaded rules, and the text of the last call
+  struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  DevBuf txt_dead, txt_cid, txt_parent, txt_el, txt_roots, txt_first, txt_names, txt_out, txt_ctl, txt_labels;
+  bool txt_labels_ok = false;
+  uint64_t arena_gen = 0;                   // counts changes of the arena (loads, reductions, frees)
+  int32_t dtext_net = -1;
+  uint64_t dtext_gen = 0;
+  uint64_t dtext_reached = 0;               // agents the text reaches
+  int64_t dtext_live = -1;                  // the net's live agents when it was rendered
+  uint64_t renders_device = 0, renders_host = 0;  // texts rendered on each side
+  std::string dtext;
   std::string err;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -450,6 +466,7 @@ inet_status upload_staged(inet_ctx* ctx) {
   ctx->st_a0 = ctx->a_bump;
   ctx->st_v0 = ctx->v_bump;
   ctx->snap_valid = false;
+  ctx->arena_gen++;
   return INET_OK;
 }
 
@@ -525,6 +542,167 @@ inet_status read_nats_device(inet_ctx* ctx, cudaStream_t st, const uint32_t* dro
   }
   k_nat_jump_gather<<<nb, 256, 0, st>>>(dval, m, ctx->jump_ctl, b0, b1);
   CK(cudaGetLastError());
+  return INET_OK;
+}
+
+// A device buffer of at least `bytes` (grown, contents dropped).
+cudaError_t dev_buf(inet_ctx::DevBuf& b, size_t bytes) {
+  if (b.cap >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  const size_t want = std::max(bytes, b.cap * 2);
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e == cudaSuccess) b.cap = want;
+  return e;
+}
+
+// The text of net `id`'s interface after ->col and ->sub, rendered on the
+// device (inet_textdev.cuh) and copied to `out`.  *ok = false when the net
+// is not a forest (a subterm reached twice, or a cycle through the
+// interface): the caller renders it on the host, whose walk bounds such
+// terms.
+inet_status read_text_device(inet_ctx* ctx, int32_t id, std::string& out, bool* ok, uint64_t* reached_out,
+                             int64_t* live_out) {
+  *ok = false;
+  *reached_out = 0;
+  *live_out = -1;
+  const NetRec& nr = ctx->nets[(size_t)id];
+  const uint32_t na = (uint32_t)ctx->a_bump, nv = (uint32_t)ctx->v_bump, nroots = (uint32_t)nr.iface.size();
+  out.clear();
+  if (nroots == 0) {
+    *ok = true;
+    return INET_OK;
+  }
+  const CompiledRules& R = ctx->rules;
+  cudaStream_t st = ctx->stream;
+  // the label table: lengths, offsets and the characters of every label
+  if (!ctx->txt_labels_ok) {
+    const size_t L = R.labels.size();
+    std::vector<uint8_t> len(kMaxLabels, 0);
+    std::vector<uint32_t> off(kMaxLabels, 0);
+    std::string chars;
+    for (size_t l = 0; l < L && l < kMaxLabels; l++) {
+      off[l] = (uint32_t)chars.size();
+      len[l] = (uint8_t)std::min<size_t>(R.labels[l].size(), 255);
+      chars.append(R.labels[l], 0, len[l]);
+    }
+    const size_t bytes = kMaxLabels * (1 + 4) + chars.size() + 16;
+    CK(dev_buf(ctx->txt_labels, bytes));
+    unsigned char* tb = static_cast<unsigned char*>(ctx->txt_labels.p);
+    CK(h2d(ctx, tb, len.data(), kMaxLabels));
+    CK(h2d(ctx, tb + kMaxLabels, off.data(), kMaxLabels * 4));
+    if (!chars.empty()) CK(h2d(ctx, tb + kMaxLabels * 5, chars.data(), chars.size()));
+    CK(cudaStreamSynchronize(st));
+    ctx->txt_labels_ok = true;
+  }
+  const uint8_t* lablen = static_cast<const uint8_t*>(ctx->txt_labels.p);
+  const uint32_t* laboff = reinterpret_cast<const uint32_t*>(lablen + kMaxLabels);
+  const char* labchars = reinterpret_cast<const char*>(lablen + kMaxLabels * 5);
+  const unsigned blocks_max = 8u * (unsigned)std::max(ctx->num_sms, 1);
+  auto grid_for = [&](uint64_t n) {
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, blocks_max));
+  };
+  // dense ids of the net's live agents
+  CK(dev_buf(ctx->txt_dead, std::max<size_t>(na, 1)));
+  CK(dev_buf(ctx->txt_cid, sizeof(uint32_t) * 2 * std::max<size_t>(na, 1)));
+  CK(dev_buf(ctx->txt_roots, sizeof(uint32_t) * nroots));
+  CK(dev_buf(ctx->txt_ctl, sizeof(uint32_t) * kTxtCtl + 2 * sizeof(TxtElem)));
+  uint8_t* dead = static_cast<uint8_t*>(ctx->txt_dead.p);
+  uint32_t* cid = static_cast<uint32_t*>(ctx->txt_cid.p);
+  uint32_t* slot = cid + std::max<size_t>(na, 1);
+  uint32_t* droots = static_cast<uint32_t*>(ctx->txt_roots.p);
+  uint32_t* ctl = static_cast<uint32_t*>(ctx->txt_ctl.p);
+  if (na) {
+    CK(cudaMemsetAsync(dead, 0, na, st));
+    CK(cudaMemsetAsync(cid, 0xFF, sizeof(uint32_t) * na, st));
+  }
+  CK(cudaMemsetAsync(ctl, 0, sizeof(uint32_t) * kTxtCtl, st));
+  CK(h2d(ctx, droots, nr.iface.data(), sizeof(uint32_t) * nroots));
+  const uint32_t net = (uint32_t)id;
+  k_txt_free_marks<<<grid_for(na), 256, 0, st>>>(ctx->dev, na, dead);
+  k_txt_compact<<<grid_for(na), 256, 0, st>>>(ctx->dev, net, na, dead, cid, slot, ctl);
+  CK(cudaGetLastError());
+  static thread_local uint32_t ncount;
+  CK(d2h(ctx, &ncount, ctl + 5, sizeof ncount));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t n_c = ncount;
+  const uint64_t n_el64 = 4ull * n_c + nroots;
+  if (n_c > na || n_el64 >= kTxtEnd) return INET_OK;  // host path
+  const uint32_t n_el = (uint32_t)n_el64;
+  CK(dev_buf(ctx->txt_parent, sizeof(uint32_t) * std::max<size_t>(n_c, 1)));
+  CK(dev_buf(ctx->txt_el, sizeof(TxtElem) * 2 * (size_t)n_el));
+  uint32_t* parent = static_cast<uint32_t*>(ctx->txt_parent.p);
+  TxtElem* b0 = static_cast<TxtElem*>(ctx->txt_el.p);
+  TxtElem* b1 = b0 + n_el;
+  if (n_c) CK(cudaMemsetAsync(parent, 0xFF, sizeof(uint32_t) * n_c, st));
+  const unsigned gel = grid_for(n_el);
+  k_txt_parent<<<grid_for(std::max(n_c, nroots)), 256, 0, st>>>(ctx->dev, n_c, na, nv, slot, cid, droots, nroots,
+                                                                ctx->dev.arity, parent, ctl);
+  k_txt_init<<<grid_for(std::max(n_c, nroots)), 256, 0, st>>>(ctx->dev, n_c, na, nv, slot, cid, droots, nroots,
+                                                              ctx->dev.arity, lablen, parent, b0, b1, ctl);
+  // the head of the list (root 0's first element) into ctl[2]
+  k_txt_head<<<1, 1, 0, st>>>(ctx->dev, n_c, na, nv, cid, droots, ctl);
+  uint32_t rounds = 1;
+  while (rounds < 64 && (1ull << rounds) < (uint64_t)n_el) rounds++;
+  for (uint32_t r = 0; r < rounds && 8 + r < (uint32_t)kTxtCtl; r++) {
+    k_txt_round<<<gel, 256, 0, st>>>(n_el, r, ctl, b0, b1);
+    k_txt_check_head<<<1, 1, 0, st>>>(n_el, r, ctl, b0, b1);
+  }
+  k_txt_copy_head<<<1, 1, 0, st>>>(ctl, b0, b1, reinterpret_cast<TxtElem*>(ctl + kTxtCtl));
+  CK(cudaGetLastError());
+  static thread_local uint32_t hctl[kTxtCtl + 2 * sizeof(TxtElem) / 4];
+  CK(d2h(ctx, hctl, ctl, sizeof(uint32_t) * kTxtCtl + sizeof(TxtElem)));
+  CK(cudaStreamSynchronize(st));
+  TxtElem he;
+  memcpy(&he, hctl + kTxtCtl, sizeof he);
+  if (hctl[0] || he.succ != kTxtEnd) return INET_OK;  // not a forest, or not ranked: host path
+  const TxtElem* fin = (hctl[1] & 1u) ? b1 : b0;
+  const unsigned long long total_chars = he.chars;
+  const uint32_t total_names = he.names;
+  unsigned long long name_chars = 0;
+  uint32_t *num = nullptr, *noff = nullptr, *nlen = nullptr;
+  if (total_names) {
+    CK(dev_buf(ctx->txt_first, sizeof(uint32_t) * std::max<size_t>(nv, 1)));
+    CK(dev_buf(ctx->txt_names, sizeof(uint32_t) * 5 * ((size_t)total_names + 1)));
+    uint32_t* first = static_cast<uint32_t*>(ctx->txt_first.p);
+    uint32_t* key = static_cast<uint32_t*>(ctx->txt_names.p);
+    uint32_t* flag = key + (total_names + 1);
+    num = flag + (total_names + 1);
+    nlen = num + (total_names + 1);
+    noff = nlen + (total_names + 1);
+    CK(cudaMemsetAsync(first, 0xFF, sizeof(uint32_t) * std::max<size_t>(nv, 1), st));
+    CK(cudaMemsetAsync(key, 0, sizeof(uint32_t) * (total_names + 1), st));
+    CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t) * (total_names + 1), st));
+    const unsigned gn = (total_names + 255) / 256;
+    k_txt_names<<<gel, 256, 0, st>>>(ctx->dev, n_el, n_c, nv, droots, slot, fin, total_names, first, key);
+    k_txt_firsts<<<gn, 256, 0, st>>>(total_names, first, key, flag);
+    k_rs_scan<<<1, 1024, 0, st>>>(flag, total_names + 1);  // exclusive: rank of each first occurrence
+    k_txt_numbers<<<gn, 256, 0, st>>>(total_names, first, key, flag, num, nlen);
+    CK(cudaMemsetAsync(nlen + total_names, 0, sizeof(uint32_t), st));
+    CK(cudaMemcpyAsync(noff, nlen, sizeof(uint32_t) * (total_names + 1), cudaMemcpyDeviceToDevice, st));
+    k_rs_scan<<<1, 1024, 0, st>>>(noff, total_names + 1);  // noff[total_names] = all name characters
+    CK(cudaGetLastError());
+    static thread_local uint32_t nc;
+    CK(d2h(ctx, &nc, noff + total_names, sizeof nc));
+    CK(cudaStreamSynchronize(st));
+    name_chars = nc;
+  }
+  const size_t len = (size_t)(total_chars + name_chars);
+  CK(dev_buf(ctx->txt_out, std::max<size_t>(len, 1)));
+  char* dout = static_cast<char*>(ctx->txt_out.p);
+  k_txt_scatter<<<gel, 256, 0, st>>>(ctx->dev, n_el, n_c, nv, droots, slot, nroots, fin, total_chars, total_names, name_chars,
+                                     num, noff, nlen, ctx->dev.arity, labchars, laboff, lablen, dout,
+                                     (unsigned long long)len, ctl);
+  CK(cudaGetLastError());
+  out.resize(len);
+  if (len) CK(d2h(ctx, &out[0], dout, len));
+  static thread_local uint32_t tail[4];
+  CK(d2h(ctx, tail, ctl, sizeof tail));
+  CK(cudaStreamSynchronize(st));
+  *ok = tail[0] == 0;
+  *reached_out = tail[3];
+  *live_out = n_c;
   return INET_OK;
 }
 
@@ -766,6 +944,9 @@ void inet_destroy(inet_ctx* ctx) {
     if (ctx->rb_host_vals) cudaFreeHost(ctx->rb_host_vals);
     if (ctx->jump_buf) cudaFree(ctx->jump_buf);
     if (ctx->jump_ctl) cudaFree(ctx->jump_ctl);
+    for (auto* b : {&ctx->txt_dead, &ctx->txt_cid, &ctx->txt_parent, &ctx->txt_el, &ctx->txt_roots, &ctx->txt_first,
+                    &ctx->txt_names, &ctx->txt_out, &ctx->txt_ctl, &ctx->txt_labels})
+      if (b->p) cudaFree(b->p);
     drop_graph(ctx);
     if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -785,6 +966,7 @@ inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len) {
   if (rc) return fail(ctx, rc, err);
   ctx->rules = std::move(r);
   ctx->have_rules = true;
+  ctx->txt_labels_ok = false;
   if (ctx->host_only) return INET_OK;
   DeviceGuard g(ctx->device);
   drop_graph(ctx);
@@ -854,6 +1036,7 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
   nr.pairs = std::move(fn.pairs);
   commit_net(ctx, id, std::move(nr), ctr);
   ctx->snap_valid = false;
+  ctx->arena_gen++;
   *net_id_out = id;
   return INET_OK;
 }
@@ -970,6 +1153,7 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
       ids_out[i] = pid[(size_t)i];
     }
     ctx->snap_valid = false;
+    ctx->arena_gen++;
     *n_loaded_out = m;
   }
   if (stop) return fail(ctx, stop, stop_msg);
@@ -1260,6 +1444,7 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   ctx->st_a0 = ctx->a_bump;
   ctx->st_v0 = ctx->v_bump;
   ctx->snap_valid = false;
+  ctx->arena_gen++;
   if (stats) {
     memset(stats, 0, sizeof *stats);
     uint64_t tot = 0;
@@ -1314,21 +1499,38 @@ inet_status inet_readback(inet_ctx* ctx, int32_t net_id, char* buf, size_t cap, 
   if (s) return s;
   if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
   DeviceGuard g(ctx->device);
-  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx)) ||
-      (s = ensure_net_counters(ctx)))
-    return s;
-  if (ctx->text_net != net_id || ctx->text_gen != ctx->snap_gen) {
-    Readback rb;
-    read_net_text(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
-                  ctx->nets[(size_t)net_id].iface, ctx->rules, rb);
-    ctx->text = std::move(rb.text);
-    ctx->text_reached = rb.reached;
-    ctx->text_net = net_id;
-    ctx->text_gen = ctx->snap_gen;
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx))) return s;
+  // rendered on the device; a net that is not a forest of terms (a
+  // subterm reached twice, a cycle) is rendered on the host, whose walk
+  // bounds it
+  if (ctx->dtext_net != net_id || ctx->dtext_gen != ctx->arena_gen) {
+    bool ok = false;
+    if ((s = read_text_device(ctx, net_id, ctx->dtext, &ok, &ctx->dtext_reached, &ctx->dtext_live))) return s;
+    if (ok) ctx->renders_device++;
+    else ctx->renders_host++;
+    if (!ok) {
+      if ((s = ensure_snapshot(ctx))) return s;
+      Readback rb;
+      read_net_text(ctx->snap_nodes.data(), ctx->snap_nodes.size(), ctx->snap_vars.data(), ctx->snap_vars.size(),
+                    ctx->nets[(size_t)net_id].iface, ctx->rules, rb);
+      ctx->dtext = std::move(rb.text);
+      ctx->dtext_reached = (uint64_t)rb.reached;
+      ctx->dtext_live = (size_t)net_id < ctx->snap_live.size() ? ctx->snap_live[(size_t)net_id] : 0;
+    }
+    ctx->dtext_net = net_id;
+    ctx->dtext_gen = ctx->arena_gen;
   }
-  if (needed_out) *needed_out = ctx->text.size() + 1;
-  if (!buf || cap < ctx->text.size() + 1) return fail(ctx, INET_ERR_INVALID_ARG, "buffer too small");
-  memcpy(buf, ctx->text.c_str(), ctx->text.size() + 1);
+  const std::string& text = ctx->dtext;
+  if (needed_out) *needed_out = text.size() + 1;
+  if (!buf || cap < text.size() + 1) return fail(ctx, INET_ERR_INVALID_ARG, "buffer too small");
+  memcpy(buf, text.c_str(), text.size() + 1);
+  return INET_OK;
+}
+
+inet_status inet_readback_counts(const inet_ctx* ctx, uint64_t* device_out, uint64_t* host_out) {
+  if (!ctx) return INET_ERR_INVALID_ARG;
+  if (device_out) *device_out = ctx->renders_device;
+  if (host_out) *host_out = ctx->renders_host;
   return INET_OK;
 }
 
@@ -1553,6 +1755,7 @@ inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
   }
   ctx->live -= (int64_t)hs[1];
   ctx->snap_valid = false;
+  ctx->arena_gen++;
   ctx->text_net = -1;
   return INET_OK;
 }
@@ -1597,14 +1800,19 @@ inet_status inet_net_info(inet_ctx* ctx, int32_t net_id, inet_net_stats* out) {
     return INET_OK;
   }
   DeviceGuard g(ctx->device);
-  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_snapshot(ctx)) ||
-      (s = ensure_net_counters(ctx)))
-    return s;
+  if ((s = ensure_workspace(ctx)) || (s = upload_staged(ctx)) || (s = ensure_net_counters(ctx))) return s;
   const unsigned long long v = ctx->h_netctr[(size_t)net_id];
   out->status = ctx->h_netstat[(size_t)net_id];
   out->interactions = v & kNetIntMask;
   out->pending_pairs = v >> kNetPairShift;
   out->reduced = nr.started && out->pending_pairs == 0 ? 1 : 0;
+  if (ctx->dtext_net == net_id && ctx->dtext_gen == ctx->arena_gen && ctx->dtext_live >= 0) {
+    // the text rendered from the current arena counted both on the device
+    out->live_agents = ctx->dtext_live;
+    out->residual_agents = ctx->dtext_live - (int64_t)ctx->dtext_reached;
+    return INET_OK;
+  }
+  if ((s = ensure_snapshot(ctx))) return s;
   uint64_t reached = ctx->text_reached;
   if (ctx->text_net != net_id || ctx->text_gen != ctx->snap_gen) {  // no text walk of this snapshot to reuse
     Readback rb;
@@ -1652,8 +1860,11 @@ inet_status inet_reset(inet_ctx* ctx) {
   ctx->step = 0;
   ctx->fcount[0] = ctx->fcount[1] = 0;
   ctx->snap_valid = false;
+  ctx->arena_gen++;
   ctx->text_net = -1;
   std::string().swap(ctx->text);
+  ctx->dtext_net = -1;
+  std::string().swap(ctx->dtext);
   ctx->tr_front.clear();
   ctx->tr_live.clear();
   ctx->poisoned = false;
