@@ -319,6 +319,26 @@ inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n);
 /* inet_free_nets() for one net. */
 inet_status inet_free_net(inet_ctx* ctx, int32_t net_id);
 
+/* Quotas: net net_ids[i] may hold at most quotas[i] live agents (0: no
+ * limit).  After each launch of inet_reduce, a net that still has active
+ * pairs and holds more agents than its quota gets INET_ERR_ARENA_FULL as its
+ * own status (inet_net_status), its pairs leave the frontier, and it counts
+ * as finished (inet_net_finished reports it; inet_free_nets can free it);
+ * every other net is untouched.  A request loop that admits nets by an
+ * estimate of their size gives each its estimate as quota, so a net that
+ * outgrows its estimate stops alone instead of filling the arena that the
+ * others share.  The arena must still hold what the nets can allocate within
+ * one launch (a time slice, slice_us).  Needs INET_ARENA_FREE_NETS (the live
+ * agents of each net are kept with the owners; else INET_ERR_STATE).  A
+ * net's quota is reset when its id is loaded again.  At most 65536 nets per
+ * call.  The paper has no counterpart. */
+inet_status inet_set_quotas(inet_ctx* ctx, const int32_t* net_ids, const uint64_t* quotas, int32_t n);
+
+/* The status of each listed net: INET_OK, INET_ERR_NO_RULE (an active pair
+ * without a rule) or INET_ERR_ARENA_FULL (over its quota), as of the end of
+ * the last inet_reduce.  The paper has no counterpart. */
+inet_status inet_net_status(inet_ctx* ctx, const int32_t* net_ids, int32_t n, int32_t* status_out);
+
 /* How much of the arena is in use (inet_arena_usage). */
 typedef struct inet_arena_usage_t {
   uint64_t agent_slots;       /* agent bump pointer: slots handed out at least once since the

@@ -154,6 +154,14 @@ class Evaluator:
         """Returns the slots and ids of finished nets for reuse (inet_free_nets)."""
         capi_lazy.inet_free_nets(self.ctx, list(net_ids))
 
+    def set_quotas(self, net_ids, quotas) -> None:
+        """Most live agents each net may hold (inet_set_quotas)."""
+        capi_lazy.inet_set_quotas(self.ctx, list(net_ids), list(quotas))
+
+    def status(self, net_ids) -> list[str]:
+        """Each net's status name: OK, NO_RULE or ARENA_FULL (over its quota)."""
+        return capi_lazy.inet_net_status(self.ctx, list(net_ids))
+
     def readback_counts(self) -> tuple[int, int]:
         """Texts inet_readback rendered on the device and on the host."""
         return capi_lazy.inet_readback_counts(self.ctx)

@@ -47,6 +47,7 @@ EXPORTED = [
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
     "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
     "inet_free_nets", "inet_free_net", "inet_arena_usage", "inet_bench_chase", "inet_readback_counts",
+    "inet_set_quotas", "inet_net_status",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -112,6 +113,8 @@ def _load():
         "inet_stage": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_nets": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_net": ([P, C.c_int32], C.c_int32),
+        "inet_set_quotas": ([P, C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.c_int32], C.c_int32),
+        "inet_net_status": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)], C.c_int32),
         "inet_readback_counts": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_arena_usage": ([P, C.POINTER(inet_arena_usage_t)], C.c_int32),
         "inet_transfer_bytes": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
@@ -244,6 +247,19 @@ def inet_free_nets(ctx, net_ids) -> None:
 
 def inet_free_net(ctx, net_id: int) -> None:
     _check(ctx, LIB.inet_free_net(ctx, net_id))
+
+
+def inet_set_quotas(ctx, net_ids, quotas) -> None:
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    q = (C.c_uint64 * len(quotas))(*quotas)
+    _check(ctx, LIB.inet_set_quotas(ctx, ids, q, len(net_ids)))
+
+
+def inet_net_status(ctx, net_ids) -> list[str]:
+    ids = (C.c_int32 * len(net_ids))(*net_ids)
+    out = (C.c_int32 * max(1, len(net_ids)))()
+    _check(ctx, LIB.inet_net_status(ctx, ids, len(net_ids), out))
+    return [STATUS_NAMES.get(out[i], out[i]) for i in range(len(net_ids))]
 
 
 def inet_readback_counts(ctx) -> tuple[int, int]:

@@ -41,9 +41,9 @@ constexpr uint32_t kMaxSolo = 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Layout {
-  size_t ctrl, node, var, vown, front0, front1, qseq, afree, vfree, netctr, netstat, netrep, netmark, hist, table,
-      tmpl, arity, trace_front, trace_live, rb_root, rb_val, fin_ids, fin_cnt, free_ids, free_st, stn_ids, stn_ctr,
-      total;
+  size_t ctrl, node, var, vown, front0, front1, qseq, afree, vfree, netctr, netstat, netrep, netmark, netlive,
+      netquota, hist, table, tmpl, arity, trace_front, trace_live, rb_root, rb_val, fin_ids, fin_cnt, free_ids, free_st,
+      stn_ids, stn_ctr, stn_live, total;
 };
 
 inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
@@ -79,6 +79,8 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.netstat = take(sizeof(int32_t) * c.max_nets);
   L.netrep = take(sizeof(uint32_t) * c.max_nets);
   L.netmark = take(c.max_nets);
+  L.netlive = take(sizeof(long long) * c.max_nets);
+  L.netquota = take(sizeof(unsigned long long) * c.max_nets);
   L.hist = take(sizeof(unsigned long long) * INET_MAX_RULES);
   L.table = take(sizeof(int16_t) * kMaxLabels * kMaxLabels);
   L.tmpl = take(sizeof(Template) * INET_MAX_RULES);
@@ -93,6 +95,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.free_st = take(sizeof(unsigned long long) * 4);
   L.stn_ids = take(sizeof(int32_t) * kReadChunk);
   L.stn_ctr = take(sizeof(unsigned long long) * kReadChunk);
+  L.stn_live = take(sizeof(long long) * kReadChunk);
   L.total = take(0) + 256;
   return L;
 }
@@ -138,6 +141,8 @@ struct inet_ctx {
   std::vector<uint32_t> st_vown;            // owning net of each staged name slot
   std::vector<unsigned long long> st_netctr;
   std::vector<int32_t> st_net_ids;          // ids of the staged nets, parallel to st_netctr
+  std::vector<long long> st_netlive;        // their agents, parallel to st_netctr
+  bool quotas_set = false;                  // some net has a quota (inet_set_quotas)
   std::vector<int32_t> free_net_ids;        // ids released by inet_free_nets, reused by loads
   // device-side per-net copies (after the last reduce)
   std::vector<unsigned long long> h_netctr;
@@ -285,6 +290,9 @@ void fill_dev(inet_ctx* ctx) {
   d.netctr = at<unsigned long long>(ctx, L.netctr);
   d.netstat = at<int32_t>(ctx, L.netstat);
   d.netrep = at<uint32_t>(ctx, L.netrep);
+  const bool track = (ctx->cfg.flags & INET_ARENA_FREE_NETS) != 0;
+  d.netlive = track ? at<long long>(ctx, L.netlive) : nullptr;
+  d.netquota = track ? at<unsigned long long>(ctx, L.netquota) : nullptr;
   d.rule_hist = at<unsigned long long>(ctx, L.hist);
   d.ctrl = at<Ctrl>(ctx, L.ctrl);
   d.table = at<int16_t>(ctx, L.table);
@@ -336,6 +344,8 @@ inet_status clear_device(inet_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netstat, 0, sizeof(int32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netrep, 0, sizeof(uint32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netmark, 0, ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.netlive, 0, sizeof(long long) * ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.netquota, 0, sizeof(unsigned long long) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
   uint32_t never = 0xFFFFFFFFu;
   CK(h2d(ctx, &ctx->dev.ctrl->stop_step, &never, 4));
@@ -391,14 +401,20 @@ inet_status upload_staged(inet_ctx* ctx) {
       CK(h2d(ctx, ctx->dev.netctr + id0, ctx->st_netctr.data(), nn * sizeof(unsigned long long)));
       CK(cudaMemsetAsync(ctx->dev.netstat + id0, 0, nn * sizeof(int32_t), ctx->stream));
       CK(cudaMemsetAsync(ctx->dev.netrep + id0, 0, nn * sizeof(uint32_t), ctx->stream));
+      if (ctx->dev.netlive) {
+        CK(h2d(ctx, ctx->dev.netlive + id0, ctx->st_netlive.data(), nn * sizeof(long long)));
+        CK(cudaMemsetAsync(ctx->dev.netquota + id0, 0, nn * sizeof(unsigned long long), ctx->stream));
+      }
     } else {
       int32_t* dids = at<int32_t>(ctx, ctx->lay.stn_ids);
       unsigned long long* dctr = at<unsigned long long>(ctx, ctx->lay.stn_ctr);
+      long long* dlive = at<long long>(ctx, ctx->lay.stn_live);
       for (size_t off = 0; off < nn; off += kReadChunk) {
         const uint32_t m = (uint32_t)std::min<size_t>(nn - off, kReadChunk);
         CK(h2d(ctx, dids, ctx->st_net_ids.data() + off, m * sizeof(int32_t)));
         CK(h2d(ctx, dctr, ctx->st_netctr.data() + off, m * sizeof(unsigned long long)));
-        k_net_ctr_scatter<<<(m + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, dids, dctr, m);
+        CK(h2d(ctx, dlive, ctx->st_netlive.data() + off, m * sizeof(long long)));
+        k_net_ctr_scatter<<<(m + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, dids, dctr, dlive, m);
         CK(cudaGetLastError());
         if (off + m < nn) CK(cudaStreamSynchronize(ctx->stream));  // the id buffers are reused
       }
@@ -463,6 +479,7 @@ inet_status upload_staged(inet_ctx* ctx) {
   ctx->st_vown.clear();
   ctx->st_netctr.clear();
   ctx->st_net_ids.clear();
+  ctx->st_netlive.clear();
   ctx->st_a0 = ctx->a_bump;
   ctx->st_v0 = ctx->v_bump;
   ctx->snap_valid = false;
@@ -838,7 +855,7 @@ int32_t peek_net_id(const inet_ctx* ctx, size_t k) {
 }
 
 // Commits net `id` (the next id peek_net_id gave) with its record.
-void commit_net(inet_ctx* ctx, int32_t id, NetRec&& nr, unsigned long long ctr) {
+void commit_net(inet_ctx* ctx, int32_t id, NetRec&& nr, unsigned long long ctr, long long agents) {
   if (!ctx->free_net_ids.empty() && ctx->free_net_ids.back() == id) {
     ctx->free_net_ids.pop_back();
     ctx->nets[(size_t)id] = std::move(nr);
@@ -851,6 +868,7 @@ void commit_net(inet_ctx* ctx, int32_t id, NetRec&& nr, unsigned long long ctr) 
   }
   ctx->st_netctr.push_back(ctr);
   ctx->st_net_ids.push_back(id);
+  ctx->st_netlive.push_back(agents);
 }
 
 // Device buffers of one control run, freed on every exit.
@@ -1034,7 +1052,7 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
   nr.iface = std::move(fn.iface);
   const unsigned long long ctr = (unsigned long long)fn.pairs.size() << kNetPairShift;
   nr.pairs = std::move(fn.pairs);
-  commit_net(ctx, id, std::move(nr), ctr);
+  commit_net(ctx, id, std::move(nr), ctr, (long long)fn.nodes.size());
   ctx->snap_valid = false;
   ctx->arena_gen++;
   *net_id_out = id;
@@ -1149,7 +1167,7 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
       nr.used = true;
       nr.iface = std::move(fn.iface);
       nr.pairs = std::move(fn.pairs);
-      commit_net(ctx, pid[(size_t)i], std::move(nr), ctr);
+      commit_net(ctx, pid[(size_t)i], std::move(nr), ctr, (long long)fn.nodes.size());
       ids_out[i] = pid[(size_t)i];
     }
     ctx->snap_valid = false;
@@ -1414,6 +1432,19 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
     }
   }
   if (!launches) CK(cudaEventRecord(ctx->ev1, ctx->stream));
+  // quotas (inet_set_quotas): a net holding more live agents than its quota
+  // stops here with INET_ERR_ARENA_FULL, its pairs leave the frontier, and
+  // the other nets go on as if it had never run
+  if (ctx->quotas_set && d.netquota) {
+    uint8_t* mark = at<uint8_t>(ctx, ctx->lay.netmark);
+    unsigned long long* hit = at<unsigned long long>(ctx, ctx->lay.free_st) + 3;
+    const uint32_t nn = (uint32_t)ctx->nets.size();
+    CK(cudaMemsetAsync(hit, 0, sizeof *hit, ctx->stream));
+    k_quota_check<<<(unsigned)std::max<uint32_t>(1, std::min<uint32_t>((nn + 255) / 256, 1024)), 256, 0, ctx->stream>>>(
+        d, nn, mark, hit);
+    k_quota_purge<<<1, 1024, 0, ctx->stream>>>(d, mark, nn, hit);
+    CK(cudaGetLastError());
+  }
   // results
   Ctrl hc;
   CK(d2h(ctx, &hc, ctx->dev.ctrl, sizeof(Ctrl)));
@@ -1762,6 +1793,46 @@ inet_status inet_free_nets(inet_ctx* ctx, const int32_t* net_ids, int32_t n) {
 
 inet_status inet_free_net(inet_ctx* ctx, int32_t net_id) { return inet_free_nets(ctx, &net_id, 1); }
 
+inet_status inet_set_quotas(inet_ctx* ctx, const int32_t* net_ids, const uint64_t* quotas, int32_t n) {
+  if (!ctx || n < 0 || (uint32_t)n > kReadChunk || (n > 0 && (!net_ids || !quotas))) return INET_ERR_INVALID_ARG;
+  if (ctx->host_only) return fail(ctx, INET_ERR_NO_DEVICE, "host-only context");
+  if (!(ctx->cfg.flags & INET_ARENA_FREE_NETS))
+    return fail(ctx, INET_ERR_STATE, "quotas need the live agents of each net: create the context with INET_ARENA_FREE_NETS");
+  for (int32_t i = 0; i < n; i++) {
+    inet_status s = check_net(ctx, net_ids[i]);
+    if (s) return s;
+  }
+  if (n == 0) return INET_OK;
+  DeviceGuard g(ctx->device);
+  inet_status s = ensure_workspace(ctx);
+  if (s) return s;
+  if ((s = upload_staged(ctx))) return s;  // a net's quota slot is reset when it is uploaded
+  int32_t* dids = at<int32_t>(ctx, ctx->lay.stn_ids);
+  unsigned long long* dq = at<unsigned long long>(ctx, ctx->lay.stn_ctr);
+  CK(h2d(ctx, dids, net_ids, sizeof(int32_t) * (size_t)n));
+  CK(h2d(ctx, dq, quotas, sizeof(uint64_t) * (size_t)n));
+  k_net_set_quota<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->dev, dids, dq, (uint32_t)n);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int32_t i = 0; i < n; i++) ctx->quotas_set = ctx->quotas_set || quotas[i] != 0;
+  return INET_OK;
+}
+
+inet_status inet_net_status(inet_ctx* ctx, const int32_t* net_ids, int32_t n, int32_t* status_out) {
+  if (!ctx || n < 0 || (n > 0 && (!net_ids || !status_out))) return INET_ERR_INVALID_ARG;
+  if (!ctx->host_only) {
+    DeviceGuard g(ctx->device);
+    const inet_status s = ensure_net_counters(ctx);
+    if (s) return s;
+  }
+  for (int32_t i = 0; i < n; i++) {
+    const int32_t id = net_ids[i];
+    if (id < 0 || (size_t)id >= ctx->nets.size() || !ctx->nets[(size_t)id].used) return INET_ERR_INVALID_ARG;
+    status_out[i] = ctx->h_netstat[(size_t)id];
+  }
+  return INET_OK;
+}
+
 inet_status inet_arena_usage(inet_ctx* ctx, inet_arena_usage_t* out) {
   if (!ctx || !out) return INET_ERR_INVALID_ARG;
   memset(out, 0, sizeof *out);
@@ -1852,6 +1923,8 @@ inet_status inet_reset(inet_ctx* ctx) {
   ctx->st_netctr.clear();
   ctx->st_vown.clear();
   ctx->st_net_ids.clear();
+  ctx->st_netlive.clear();
+  ctx->quotas_set = false;
   ctx->free_net_ids.clear();
   ctx->rb_ids.clear();
   ctx->a_bump = ctx->v_bump = 0;

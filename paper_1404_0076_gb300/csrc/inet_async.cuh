@@ -395,6 +395,11 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
   if (valid) {
     atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)np - 1) << kNetPairShift));
     atomicAdd(&hist[hdr >> 24], 1u);
+    // live agents of the net (its quota is checked between launches)
+    if constexpr (kTrack) {
+      if (n_new != 2) atomicAdd(reinterpret_cast<unsigned long long*>(d.netlive + net),
+                                (unsigned long long)((long long)n_new - 2));
+    }
   }
   return valid ? np : 0u;
 }

@@ -112,11 +112,14 @@ __global__ void k_free_unmark(Dev d, const int32_t* ids, uint32_t n, uint8_t* ma
   d.netctr[id] = 0;
   d.netstat[id] = 0;
   d.netrep[id] = 1;
+  d.netlive[id] = 0;
+  d.netquota[id] = 0;
 }
 
 // Per-net counters of newly uploaded nets whose ids are not one run:
-// (id, counter) pairs, status and reported flag cleared.
-__global__ void k_net_ctr_scatter(Dev d, const int32_t* ids, const unsigned long long* ctr, uint32_t n) {
+// (id, counter, live agents), status, reported flag and quota cleared.
+__global__ void k_net_ctr_scatter(Dev d, const int32_t* ids, const unsigned long long* ctr, const long long* live,
+                                  uint32_t n) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t id = ids[i];
@@ -127,6 +130,78 @@ __global__ void k_net_ctr_scatter(Dev d, const int32_t* ids, const unsigned long
   d.netctr[id] = ctr[i];
   d.netstat[id] = 0;
   d.netrep[id] = 0;
+  if (d.netlive) {
+    d.netlive[id] = live[i];
+    d.netquota[id] = 0;
+  }
+}
+
+// netquota[ids[i]] = q[i].
+__global__ void k_net_set_quota(Dev d, const int32_t* ids, const unsigned long long* q, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && ids[i] >= 0 && (uint32_t)ids[i] < d.max_nets) d.netquota[ids[i]] = q[i];
+}
+
+// Quotas, between launches: a net that still has active pairs and holds
+// more live agents than its quota gets INET_ERR_ARENA_FULL as its status and
+// is marked for k_quota_purge; *hit counts them.  Other nets are untouched.
+__global__ void k_quota_check(Dev d, uint32_t n_nets, uint8_t* mark, unsigned long long* hit) {
+  for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nets; n += gridDim.x * blockDim.x) {
+    const unsigned long long q = d.netquota[n];
+    if (!q || d.netlive[n] <= (long long)q || (d.netctr[n] >> kNetPairShift) == 0) continue;
+    atomicCAS(d.netstat + n, 0, INET_ERR_ARENA_FULL);
+    mark[n] = 1;
+    atomicAdd(hit, 1ull);
+  }
+}
+
+// One block: the frontier `cur` loses the pairs of marked nets (compacted in
+// place, chunk by chunk: every write lands below the chunk being read), and
+// those nets count no pending pair any more, so they are finished (with
+// their error status) and can be freed.
+__global__ void k_quota_purge(Dev d, uint8_t* mark, uint32_t n_nets, const unsigned long long* hit) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t kept;
+  if (*hit == 0) return;  // no net went over its quota
+  Ctrl* c = d.ctrl;
+  const uint32_t cur = c->step & 1u;
+  const uint32_t n = min(c->fcount[cur], d.cap_pairs);
+  Pair* f = d.front[cur];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t wr = 0;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    Pair p{0, 0};
+    bool keep = false;
+    if (i < n) {
+      p = f[i];
+      keep = true;
+      if (p.a < d.cap_agents) {
+        const uint32_t net = (uint32_t)__ldcg(&d.node[p.a].head) >> 8;
+        if (net < n_nets && mark[net]) keep = false;
+      }
+    }
+    const unsigned m = __ballot_sync(kFull, keep);
+    if (lane == 0) wsum[wid] = __popc(m);
+    __syncthreads();  // every pair of the chunk has been read, the warp counts are there
+    uint32_t before = 0;
+    for (int w = 0; w < wid; w++) before += wsum[w];
+    if (keep) f[wr + before + __popc(m & lanemask_lt())] = p;
+    if (threadIdx.x == 0) {
+      uint32_t t = 0;
+      for (int w = 0; w < nw; w++) t += wsum[w];
+      kept = t;
+    }
+    __syncthreads();
+    wr += kept;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) c->fcount[cur] = wr;
+  for (uint32_t k = threadIdx.x; k < n_nets; k += blockDim.x) {
+    if (!mark[k]) continue;
+    d.netctr[k] &= kNetIntMask;
+    mark[k] = 0;
+  }
 }
 
 // Placement, step 1 (one thread): publish both rings (between reductions

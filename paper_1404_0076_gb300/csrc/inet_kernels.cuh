@@ -89,6 +89,8 @@ struct Dev {
   unsigned long long* netctr;
   int32_t* netstat;
   uint32_t* netrep;      // 1 once inet_net_finished reported the net
+  long long* netlive;    // live agents of each net (kept with owner tracking only)
+  unsigned long long* netquota;  // most live agents a net may hold (0: no limit; owner tracking only)
   uint32_t paper;        // the paper's loop form: name equations go to `eq_fix` instead of being linked
   unsigned long long* eq;  // equations t | u << 32 of the paper's form (communication phase)
   uint32_t* eq_n;
@@ -608,6 +610,11 @@ __device__ void process_chunk(const Dev& d, const Smem& s, uint32_t base, uint32
                                       ((unsigned long long)((long long)tp - (long long)cnt) << kNetPairShift));
     } else {
       atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)pushed - 1) << kNetPairShift));
+    }
+    // live agents of the net (its quota is checked between launches)
+    if constexpr (kTrack) {
+      if (n_new != 2) atomicAdd(reinterpret_cast<unsigned long long*>(d.netlive + net),
+                                (unsigned long long)((long long)n_new - 2));
     }
     const unsigned rp = __match_any_sync(vm, (unsigned)T.rule);
     if (lane == __ffs(rp) - 1) atomicAdd(&s.hist[T.rule], (uint32_t)__popc(rp));

@@ -17,7 +17,10 @@ back (inet_free_nets returns its agent and name slots and its id), and later
 requests are placed into the freed slots, so a long request holds only its
 own memory.  Frees are batched (one scan of the arena frees many nets): when
 the nets waiting to be freed hold a sixteenth of the arena, when net ids run
-short, or when a request does not fit.
+short, or when a request does not fit.  Each admitted net gets its footprint
+estimate as its quota (inet_set_quotas): a request that outgrows its
+estimate stops alone with ARENA_FULL at the next epoch boundary, and the
+others, whose estimates admission reserved, are untouched.
 """
 from __future__ import annotations
 
@@ -54,7 +57,7 @@ def default_footprint(text: str, size: int) -> int:
 class Server:
     def __init__(self, rules: str, device: int = 0, budget_bytes: int = 2 << 30, epoch_us: int = 1000,
                  max_nets: int = 1 << 15, max_pairs: int = 1 << 22, block: int = 0, grid: int = 0,
-                 footprint=default_footprint, make_evaluator=None):
+                 footprint=default_footprint, make_evaluator=None, quotas: bool = True):
         # per agent slot: 16-byte record + 4-byte ring entry; per name slot:
         # 4 (slot) + 4 (ring entry) + 4 (owner); per pair: 2 x 8 frontier + 8 sequence
         rest = max(budget_bytes - 24 * max_pairs, 1 << 20)
@@ -72,6 +75,7 @@ class Server:
         self.epoch_us = epoch_us
         self.block, self.grid = block, grid
         self.footprint = footprint
+        self.quotas = quotas        # each net may hold at most its footprint estimate
         self.used = 0               # estimated agent slots of admitted nets not freed yet
         self.inflight = {}          # net id -> (rid, arrival, admitted, need)
         self.unstaged = []          # admitted nets not yet handed to the device
@@ -134,6 +138,8 @@ class Server:
             return 0
         t0 = time.perf_counter()
         nids = self.ev.load_nets([t for _, t, _, _ in take])
+        if self.quotas:
+            self.ev.set_quotas(nids, needs)
         self.host_s["load"] += time.perf_counter() - t0
         for (rid, _, _, arrival), need, nid in zip(take, needs, nids):
             self.unstaged.append(nid)
@@ -206,11 +212,12 @@ class Server:
                 return out
             vals, ints = r
             t = now_fn()
-            for nid, v, n in zip(self.rb_batch, vals, ints):
+            stats = ev.status(self.rb_batch) if self.quotas else ["OK"] * len(self.rb_batch)
+            for nid, v, n, stt in zip(self.rb_batch, vals, ints, stats):
                 rid, arr, adm, need = self.inflight.pop(nid)
                 self.to_free.append(nid)
                 self.free_need += need
-                out.append(Finished(rid, arr, adm, t, v, n))
+                out.append(Finished(rid, arr, adm, t, v, n, stt))
             self.rb_batch = None
         if self.ready:
             batch, self.ready = self.ready[:65536], self.ready[65536:]

@@ -177,6 +177,34 @@ def test_free_errors_leave_everything_in_place(orc):
     ev.close()
 
 
+def test_quota_stops_one_net_only(orc):
+    nets = [W.fib_net(18), W.mul_net(9, 11), W.add_net(50, 7)]
+    exp = orc.run(R, nets)
+    ev = make_ev(max_agents=1 << 20, max_vars=1 << 20, max_pairs=1 << 16, max_nets=64)
+    ev.load_rules(R)
+    ids = ev.load_nets(nets)
+    # Fibonacci(18) peaks far above 500 live agents; the others far below
+    # their quotas
+    ev.set_quotas(ids, [500, 1 << 20, 0])
+    ev.stage(ids)
+    for _ in range(1000):
+        st = ev.reduce([], mode="async", slice_us=100, check=False)
+        if st["status"] == "OK" or ids[0] in ev.finished():
+            break
+    ev.reduce([], mode="async")
+    assert ev.status(ids) == ["ARENA_FULL", "OK", "OK"]
+    assert ev.pending(ids) == [0, 0, 0]
+    check_against(ev, ids[1:], exp[1:])
+    ev.free(ids)
+    use = ev.arena_usage()
+    assert use["live_agents"] == 0 and use["free_agent_slots"] == use["agent_slots"]
+    # the context goes on: the same net without a quota reduces correctly
+    i = ev.load_net(nets[0])
+    ev.reduce([i], mode="async")
+    check_against(ev, [i], exp[:1])
+    ev.close()
+
+
 def test_free_needs_owner_tracking(orc):
     from paper_1404_0076_gb300 import Evaluator, InetError
     with Evaluator(device=0, max_agents=1 << 16, max_vars=1 << 16, max_pairs=1 << 12, max_nets=16) as ev:

@@ -53,6 +53,12 @@ class FakeEvaluator:
     def load_nets(self, texts):
         return [self.load_net(t) for t in texts]
 
+    def set_quotas(self, ids, quotas):
+        pass
+
+    def status(self, ids):
+        return ["OK"] * len(ids)
+
     def free(self, ids):
         for i in ids:
             assert self.left[i] == 0 and i not in (self.batch or [])
@@ -197,6 +203,33 @@ def test_results_in_the_mix_equal_results_alone(oracle):
     # another one was still in flight
     spans = sorted((d.admitted, d.finished) for d in done)
     assert any(b[0] < a[1] for a, b in zip(spans, spans[1:]))
+
+
+@pytest.mark.gpu
+def test_an_underestimated_request_fails_alone(oracle):
+    """One request claims a footprint far below what it builds: it stops with
+    ARENA_FULL at an epoch boundary (its quota), and every other request in
+    the mix completes exactly as alone; the arena is never poisoned."""
+    reqs = mixed_requests(300, seed=14040076 + 6)
+    bad = len(reqs) // 3
+    reqs[bad] = Req(reqs[bad].arrival_s, W.fib_net(19), 3000)   # peaks near 20 000 live agents
+
+    def footprint(text, size):
+        return 40 if text == reqs[bad].net else default_footprint(text, size)
+    srv = Server(W.ARITH_RULES, budget_bytes=256 << 20, epoch_us=300, max_pairs=1 << 16, footprint=footprint)
+    try:
+        done = srv.serve(reqs)
+    finally:
+        srv.close()
+    assert sorted(d.rid for d in done) == list(range(len(reqs)))
+    assert srv.resets == 0
+    alone = oracle.run(W.ARITH_RULES, [r.net for r in reqs], quiet=True, threads=8)
+    for d in done:
+        if d.rid == bad:
+            assert d.status == "ARENA_FULL", d
+            continue
+        assert d.status == "OK", d
+        assert (d.value, d.interactions) == (alone[d.rid]["nat"], alone[d.rid]["interactions"]), d.rid
 
 
 def test_summary_percentiles_on_cpu():
