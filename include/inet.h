@@ -264,15 +264,15 @@ inet_status inet_net_pending(inet_ctx* ctx, const int32_t* net_ids, int32_t n, u
 inet_status inet_net_finished(inet_ctx* ctx, int32_t* ids_out, int32_t cap, int32_t* n_out);
 
 /* inet_readback_nat() for many nets at once, on the device, following name
- * slots as ->col/->sub do (Theorem 1): one thread walks each net for a
- * bounded number of elements (128 on a small arena, more on a large one,
- * where ranking costs more); numerals that are longer are finished by list
- * ranking (pointer jumping over every agent and name slot of the arena).
- * values_out[i] = k when net i's interface is one numeral S^k(Z), else
- * UINT64_MAX; interactions_out (may be NULL) gets each net's interaction
- * count.  Copies only 16 bytes per net to the host.  The first call, and
- * the first after the arena has grown, allocates the ranking scratch
- * (16 bytes per agent and name slot in use) with cudaMalloc. */
+ * slots as ->col/->sub do (Theorem 1): one thread walks each net for 256 S
+ * agents; numerals that are longer are finished by list ranking: one scan
+ * of the agent slots lists the agents of those nets (each record names its
+ * net), and pointer jumping runs over that list only.  values_out[i] = k
+ * when net i's interface is one numeral S^k(Z), else UINT64_MAX;
+ * interactions_out (may be NULL) gets each net's interaction count.  Copies
+ * only 16 bytes per net to the host.  The first call, and the first after
+ * the arena has grown, allocates the ranking scratch (20 bytes per agent
+ * slot in use) with cudaMalloc. */
 inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n, uint64_t* values_out,
                                uint64_t* interactions_out);
 

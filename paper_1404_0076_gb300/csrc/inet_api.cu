@@ -29,8 +29,7 @@ namespace {
 
 constexpr uint32_t kTraceCap = 1u << 20;
 constexpr uint32_t kReadChunk = 1u << 16;  // nets per device walk of inet_readback_nats
-constexpr uint32_t kWalkMin = 128;         // elements one thread walks at least before the arena is ranked
-constexpr uint32_t kWalkMax = 1u << 20;
+constexpr uint32_t kWalkMin = 256;         // S agents one thread walks before its net's agents are ranked
 constexpr uint64_t kDefaultAgents = 1ull << 22;
 constexpr uint64_t kDefaultVars = 1ull << 22;
 constexpr uint64_t kDefaultPairs = 1ull << 21;
@@ -43,7 +42,7 @@ constexpr size_t kMaxSmem = 227 * 1024;
 struct Layout {
   size_t ctrl, node, var, vown, front0, front1, qseq, afree, vfree, netctr, netstat, netrep, netmark, netlive,
       netquota, hist, table, tmpl, arity, trace_front, trace_live, rb_root, rb_val, fin_ids, fin_cnt, free_ids, free_st,
-      stn_ids, stn_ctr, stn_live, total;
+      stn_ids, stn_ctr, stn_live, rbmark, total;
 };
 
 inet_arena_cfg with_defaults(const inet_arena_cfg* in) {
@@ -96,6 +95,7 @@ Layout layout_of(const inet_arena_cfg& c) {
   L.stn_ids = take(sizeof(int32_t) * kReadChunk);
   L.stn_ctr = take(sizeof(unsigned long long) * kReadChunk);
   L.stn_live = take(sizeof(long long) * kReadChunk);
+  L.rbmark = take(c.max_nets);
   L.total = take(0) + 256;
   return L;
 }
@@ -344,6 +344,7 @@ inet_status clear_device(inet_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netstat, 0, sizeof(int32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netrep, 0, sizeof(uint32_t) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netmark, 0, ctx->cfg.max_nets, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.rbmark, 0, ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netlive, 0, sizeof(long long) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.netquota, 0, sizeof(unsigned long long) * ctx->cfg.max_nets, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.hist, 0, sizeof(unsigned long long) * INET_MAX_RULES, ctx->stream));
@@ -512,52 +513,44 @@ inet_status ensure_net_counters(inet_ctx* ctx) {
 // counters hold every element of their lists.  No readback may be in
 // flight when the scratch grows.
 inet_status read_nats_device(inet_ctx* ctx, cudaStream_t st, const uint32_t* droot, uint32_t m, int s_label,
-                             int z_label, unsigned long long* dval, double rank_weight) {
+                             int z_label, unsigned long long* dval) {
   const uint32_t na = (uint32_t)ctx->a_bump, nv = (uint32_t)ctx->v_bump;
-  const uint64_t n_slots = (uint64_t)na + nv;
   if (!ctx->jump_ctl) CK(cudaMalloc(&ctx->jump_ctl, sizeof(uint32_t) * kJumpCtl));
-  if (n_slots > ctx->jump_cap) {
-    const uint64_t want = std::min<uint64_t>(std::max<uint64_t>(n_slots, 2 * ctx->jump_cap),
-                                             ctx->cfg.max_agents + ctx->cfg.max_vars);
+  if (na > ctx->jump_cap) {
+    // (successor, weight) twice and the list, per agent slot in use
+    const uint64_t want = std::min<uint64_t>(std::max<uint64_t>(na, 2 * ctx->jump_cap), ctx->cfg.max_agents);
     if (ctx->jump_buf) CK(cudaFree(ctx->jump_buf));
     ctx->jump_buf = nullptr;
     ctx->jump_cap = 0;
-    CK(cudaMalloc(&ctx->jump_buf, sizeof(uint2) * 2 * want));
+    CK(cudaMalloc(&ctx->jump_buf, (sizeof(uint2) * 2 + sizeof(uint32_t)) * want));
     ctx->jump_cap = want;
   }
   uint2* b0 = ctx->jump_buf;
   uint2* b1 = ctx->jump_buf + ctx->jump_cap;
-  CK(cudaMemsetAsync(ctx->jump_ctl, 0, sizeof(uint32_t) * kJumpCtl, st));
+  uint32_t* lst = reinterpret_cast<uint32_t*>(ctx->jump_buf + 2 * ctx->jump_cap);
+  uint32_t* ctl = ctx->jump_ctl;
+  uint32_t* cnt = ctl + kJumpCtl - 1;
+  uint8_t* mark = at<uint8_t>(ctx, ctx->lay.rbmark);
+  CK(cudaMemsetAsync(ctl, 0, sizeof(uint32_t) * kJumpCtl, st));
   const unsigned nb = (m + 255) / 256;
-  // The walk's budget, as in ski rental: keep walking while the walk costs
-  // less than ranking would (about 0.75 us per element of the longest
-  // numeral against about 4 ps per slot of the arena and round, plus a few
-  // microseconds per round, at least log2(budget) rounds), so the two
-  // together cost at most about twice the cheaper one.  rank_weight scales
-  // the ranking's cost: below 1 when the caller waits and the GPU has
-  // nothing else to do, 1 when reductions run beside the readback and the
-  // ranking's traffic slows them.  A small arena is ranked after kWalkMin
-  // elements; a large one (a serving arena) is walked further.
-  uint32_t budget = kWalkMin;
-  for (uint32_t lg = 7; budget < kWalkMax; budget *= 2, lg++) {
-    const double walk_s = 0.75e-6 * budget, rank_s = rank_weight * lg * (4e-12 * (double)n_slots + 5e-6);
-    if (walk_s >= rank_s) break;
-  }
-  k_nat_walk<<<nb, 256, 0, st>>>(ctx->dev, droot, m, na, nv, s_label, z_label, budget, dval, ctx->jump_ctl);
+  // every net is walked for kWalkMin S agents; the rest of each longer
+  // numeral is ranked on a list of its net's agents only
+  k_nat_walk<<<nb, 256, 0, st>>>(ctx->dev, droot, m, na, nv, s_label, z_label, kWalkMin, dval, ctl);
   CK(cudaGetLastError());
-  if (n_slots == 0) return INET_OK;
-  const unsigned grid =
-      (unsigned)std::min<uint64_t>((n_slots + 255) / 256, 8ull * (uint64_t)std::max(ctx->num_sms, 1));
-  k_nat_jump_init<<<grid, 256, 0, st>>>(ctx->dev, na, nv, s_label, z_label, ctx->jump_ctl, b0);
+  if (na == 0) return INET_OK;
+  const unsigned grid = (unsigned)std::min<uint64_t>((na + 255) / 256, 8ull * (uint64_t)std::max(ctx->num_sms, 1));
+  k_nat_mark<<<nb, 256, 0, st>>>(ctx->dev, dval, m, na, mark);
+  k_nat_list<<<grid, 256, 0, st>>>(ctx->dev, na, nv, s_label, z_label, mark, ctl, lst, cnt, b0);
   CK(cudaGetLastError());
-  // a list of L elements is ranked after ceil(log2 L) rounds, L <= n_slots
+  // a list of L agents is ranked after ceil(log2 L) rounds, L <= na
   uint32_t rounds = 1;
-  while ((1ull << rounds) < n_slots) rounds++;
+  while ((1ull << rounds) < na && rounds < (uint32_t)kJumpCtl - 4) rounds++;
   for (uint32_t r = 0; r < rounds; r++) {
-    k_nat_jump_round<<<grid, 256, 0, st>>>((uint32_t)n_slots, r, ctx->jump_ctl, b0, b1);
-    k_nat_jump_check<<<nb, 256, 0, st>>>(dval, m, (uint32_t)n_slots, r, ctx->jump_ctl, b0, b1);
+    k_nat_lround<<<grid, 256, 0, st>>>(na, r, ctl, lst, cnt, b0, b1);
+    k_nat_jump_check<<<nb, 256, 0, st>>>(dval, m, na, r, ctl, b0, b1);
   }
-  k_nat_jump_gather<<<nb, 256, 0, st>>>(dval, m, ctx->jump_ctl, b0, b1);
+  k_nat_unmark<<<nb, 256, 0, st>>>(ctx->dev, dval, m, na, mark);
+  k_nat_jump_gather<<<nb, 256, 0, st>>>(dval, m, na, ctl, b0, b1);
   CK(cudaGetLastError());
   return INET_OK;
 }
@@ -1628,7 +1621,7 @@ inet_status inet_readback_nats(inet_ctx* ctx, const int32_t* net_ids, int32_t n,
     uint32_t* droot = at<uint32_t>(ctx, ctx->lay.rb_root);
     unsigned long long* dval = at<unsigned long long>(ctx, ctx->lay.rb_val);
     CK(h2d(ctx, droot, roots.data() + off, sizeof(uint32_t) * (size_t)m));
-    if ((s = read_nats_device(ctx, ctx->stream, droot, (uint32_t)m, si->second, zi->second, dval, 0.25))) return s;
+    if ((s = read_nats_device(ctx, ctx->stream, droot, (uint32_t)m, si->second, zi->second, dval))) return s;
     CK(d2h(ctx, values_out + off, dval, sizeof(unsigned long long) * (size_t)m));
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1673,7 +1666,7 @@ inet_status inet_readback_nats_begin(inet_ctx* ctx, const int32_t* net_ids, int3
     CK(cudaStreamWaitEvent(ctx->rb_stream, ctx->rb_after, 0));
     CK(cudaMemcpyAsync(droot, ctx->rb_host_roots, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
                        ctx->rb_stream));
-    if ((s = read_nats_device(ctx, ctx->rb_stream, droot, (uint32_t)n, si->second, zi->second, dval, 1.0))) return s;
+    if ((s = read_nats_device(ctx, ctx->rb_stream, droot, (uint32_t)n, si->second, zi->second, dval))) return s;
     CK(cudaMemcpyAsync(ctx->rb_host_vals, dval, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToHost,
                        ctx->rb_stream));
     CK(cudaEventRecord(ctx->rb_ready, ctx->rb_stream));

@@ -40,6 +40,7 @@ class Finished:
     value: int | None   # numeral result, None if the interface is not S^k(Z)
     interactions: int
     status: str = "OK"
+    detected: float = 0.0  # when the device scan reported the net finished (before its readback)
 
     @property
     def latency(self) -> float:
@@ -81,6 +82,7 @@ class Server:
         self.unstaged = []          # admitted nets not yet handed to the device
         self.running = 0            # admitted nets not finished yet
         self.ready = []             # finished, readback not yet begun
+        self.detected = {}          # net id -> when the device scan reported it finished
         self.rb_batch = None        # nets of the readback in flight
         self.to_free = []           # read back, waiting to be freed
         self.free_need = 0          # their estimated slots
@@ -178,6 +180,10 @@ class Server:
             fin = [nid for nid in ev.finished() if nid in self.inflight]
             self.running -= len(fin)
             self.ready.extend(fin)
+            if fin:
+                td = now_fn()
+                for nid in fin:
+                    self.detected[nid] = td
             self.host_s["finished"] += clk() - t2
         t3 = clk()
         done.extend(self._harvest(now_fn, wait=False))
@@ -201,6 +207,7 @@ class Server:
         self.rb_batch = None
         self.to_free = []
         self.free_need = 0
+        self.detected = {}
 
     def _harvest(self, now_fn, wait: bool) -> list[Finished]:
         """Completes the readback in flight (if done) and begins the next."""
@@ -217,7 +224,7 @@ class Server:
                 rid, arr, adm, need = self.inflight.pop(nid)
                 self.to_free.append(nid)
                 self.free_need += need
-                out.append(Finished(rid, arr, adm, t, v, n, stt))
+                out.append(Finished(rid, arr, adm, t, v, n, stt, self.detected.pop(nid, t)))
             self.rb_batch = None
         if self.ready:
             batch, self.ready = self.ready[:65536], self.ready[65536:]
@@ -283,6 +290,8 @@ def summarize(done: list[Finished], wall_s: float) -> dict:
     lat = sorted(f.latency for f in done)
     wait = sorted(f.admitted - f.arrival for f in done)
     serv = sorted(f.finished - f.admitted for f in done)
+    comp = sorted(f.detected - f.admitted for f in done if f.detected)
+    rdbk = sorted(f.finished - f.detected for f in done if f.detected)
 
     def ms(x):
         return None if x is None else 1e3 * x
@@ -292,6 +301,9 @@ def summarize(done: list[Finished], wall_s: float) -> dict:
             "mean_ms": ms(sum(lat) / len(lat)) if lat else None,
             "admission_wait_p50_ms": ms(_pct(wait, 50)), "admission_wait_p99_ms": ms(_pct(wait, 99)),
             "service_p50_ms": ms(_pct(serv, 50)), "service_p99_ms": ms(_pct(serv, 99)),
+            # service = reduction (admitted to reported finished) + readback
+            "reduce_p50_ms": ms(_pct(comp, 50)), "reduce_p99_ms": ms(_pct(comp, 99)),
+            "readback_p50_ms": ms(_pct(rdbk, 50)), "readback_p99_ms": ms(_pct(rdbk, 99)),
             "interactions": ints, "interactions_per_s": ints / wall_s if wall_s > 0 else None,
             "failed": sum(1 for f in done if f.status != "OK")}
 

@@ -485,7 +485,7 @@ def long_readback_nets():
     nonnat = "< r | r = " + "S(" * 300 + "Add(Z, x)" + ")" * 300 + ", x = Z >"
     return [W.add_net(3000, 7), W.mul_net(40, 50), W.add_net(0, 129), W.add_net(128, 0), W.add_net(127, 1),
             W.add_net(63, 1), chain, nonnat, "< a, b | Add(a, b) = Z >", W.add_net(1, 1), W.fib_net(18),
-            W.add_net(0, 0)]
+            W.add_net(0, 0), W.add_net(0, 257), W.add_net(256, 0), W.add_net(255, 1), W.add_net(254, 1)]
 
 
 @pytest.mark.parametrize("mode", ["async", "persistent"])
