@@ -37,6 +37,7 @@ extern "C" {
 #endif
 
 typedef struct inet_ctx inet_ctx;
+typedef struct inet_parsed inet_parsed;
 typedef int32_t inet_status;
 
 enum {
@@ -203,6 +204,28 @@ inet_status inet_load_net(inet_ctx* ctx, const char* text, size_t len, int32_t* 
  * is returned) with *n_loaded_out = the number of nets loaded before it. */
 inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offsets, int32_t n, int32_t* ids_out,
                            int32_t* n_loaded_out);
+
+/* inet_load_nets() in two halves, so that parsing can overlap the device
+ * work of the context: inet_parse_nets parses and flattens n nets (net i
+ * is buf[offsets[i] .. offsets[i+1])) with the context's rule set only, on
+ * the process-wide pool of host threads, into a new batch *out that the
+ * caller frees with inet_parsed_free.  It reads nothing of the context but
+ * its rules, so it may run on another host thread while the context is in
+ * use (the rules must not change meanwhile).  Parse errors are kept per net
+ * and reported when that net is loaded.  inet_load_parsed then places nets
+ * [first, first + n) of the batch in the context like inet_load_nets (ids,
+ * capacity checks, staging; the first net that fails stops it, with
+ * *n_loaded_out the nets loaded before it); each net of a batch can be
+ * loaded once (INET_ERR_INVALID_ARG otherwise), and only into a context
+ * with the same rule set (INET_ERR_STATE otherwise).  inet_parsed_info
+ * gives the nets in the batch and their agents in total (either pointer
+ * may be NULL).  The paper has no counterpart. */
+inet_status inet_parse_nets(const inet_ctx* ctx, const char* buf, const uint64_t* offsets, int32_t n,
+                            inet_parsed** out);
+inet_status inet_parsed_info(const inet_parsed* p, int32_t* n_out, uint64_t* agents_out);
+inet_status inet_load_parsed(inet_ctx* ctx, inet_parsed* p, int32_t first, int32_t n, int32_t* ids_out,
+                             int32_t* n_loaded_out);
+void inet_parsed_free(inet_parsed* p);
 
 /* Adds the active pairs of the listed nets (which must not have been
  * staged or reduced yet; n may be 0) to the frontier and runs the reduction loop of

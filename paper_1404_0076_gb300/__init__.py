@@ -44,6 +44,19 @@ class _Lazy:
 capi_lazy = _Lazy()
 
 
+class Parsed:
+    """A batch of nets parsed by Evaluator.parse; freed when dropped."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.n = capi_lazy.inet_parsed_info(handle)[0]
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            capi_lazy.inet_parsed_free(self.handle)
+            self.handle = None
+
+
 class Evaluator:
     """One evaluation context on one GPU (device < 0: host-only, for parsing
     and loading without a GPU).
@@ -102,6 +115,15 @@ class Evaluator:
 
     def load_net(self, text: str) -> int:
         return capi_lazy.inet_load_net(self.ctx, text)
+
+    def parse(self, texts) -> "Parsed":
+        """Parses nets apart from the context (inet_parse_nets): another
+        thread may do this while the context reduces."""
+        return Parsed(capi_lazy.inet_parse_nets(self.ctx, list(texts)))
+
+    def load_parsed(self, parsed: "Parsed", first: int, n: int) -> list[int]:
+        """Places nets [first, first + n) of a parsed batch (inet_load_parsed)."""
+        return capi_lazy.inet_load_parsed(self.ctx, parsed.handle, first, n)
 
     def load_nets(self, texts) -> list[int]:
         return capi_lazy.inet_load_nets(self.ctx, list(texts))

@@ -47,7 +47,8 @@ EXPORTED = [
     "inet_readback_nats", "inet_readback_nats_begin", "inet_readback_nats_end", "inet_bench_exch",
     "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
     "inet_free_nets", "inet_free_net", "inet_arena_usage", "inet_bench_chase", "inet_readback_counts",
-    "inet_set_quotas", "inet_net_status",
+    "inet_set_quotas", "inet_net_status", "inet_parse_nets", "inet_parsed_info", "inet_load_parsed",
+    "inet_parsed_free",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -114,6 +115,10 @@ def _load():
         "inet_free_nets": ([P, C.POINTER(C.c_int32), C.c_int32], C.c_int32),
         "inet_free_net": ([P, C.c_int32], C.c_int32),
         "inet_set_quotas": ([P, C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.c_int32], C.c_int32),
+        "inet_parse_nets": ([P, C.c_char_p, C.POINTER(C.c_uint64), C.c_int32, C.POINTER(P)], C.c_int32),
+        "inet_parsed_info": ([P, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)], C.c_int32),
+        "inet_load_parsed": ([P, P, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int32),
+        "inet_parsed_free": ([P], None),
         "inet_net_status": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)], C.c_int32),
         "inet_readback_counts": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_arena_usage": ([P, C.POINTER(inet_arena_usage_t)], C.c_int32),
@@ -213,6 +218,34 @@ def inet_load_nets(ctx, texts) -> list[int]:
     done = C.c_int32()
     _check(ctx, LIB.inet_load_nets(ctx, b"".join(enc), offs, n, ids, C.byref(done)))
     return list(ids[:n])
+
+
+def inet_parse_nets(ctx, texts) -> C.c_void_p:
+    """Parses nets apart from the context (may run on another thread); the
+    batch is freed with inet_parsed_free."""
+    enc = [t.encode() for t in texts]
+    n = len(enc)
+    offs = (C.c_uint64 * (n + 1))(0, *itertools.accumulate(map(len, enc)))
+    out = C.c_void_p()
+    _check(None, LIB.inet_parse_nets(ctx, b"".join(enc), offs, n, C.byref(out)))
+    return out
+
+
+def inet_parsed_info(p) -> tuple[int, int]:
+    n, a = C.c_int32(), C.c_uint64()
+    _check(None, LIB.inet_parsed_info(p, C.byref(n), C.byref(a)))
+    return n.value, a.value
+
+
+def inet_load_parsed(ctx, p, first: int, n: int) -> list[int]:
+    ids = (C.c_int32 * max(1, n))()
+    done = C.c_int32()
+    _check(ctx, LIB.inet_load_parsed(ctx, p, first, n, ids, C.byref(done)))
+    return list(ids[:n])
+
+
+def inet_parsed_free(p) -> None:
+    LIB.inet_parsed_free(p)
 
 
 def inet_load_net(ctx, text: str) -> int:

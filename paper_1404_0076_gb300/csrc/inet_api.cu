@@ -126,6 +126,7 @@ struct inet_ctx {
   // rules
   bool have_rules = false;
   CompiledRules rules;
+  uint64_t rules_gen = 0;                   // counts rule sets loaded
   // host mirrors of device counters
   uint64_t a_bump = 0, v_bump = 0;
   int64_t live = 0;
@@ -864,6 +865,147 @@ void commit_net(inet_ctx* ctx, int32_t id, NetRec&& nr, unsigned long long ctr, 
   ctx->st_netlive.push_back(agents);
 }
 
+// A batch of nets parsed and flattened on their own (agent and name slots
+// from 0, net id 0), ready to be placed in a context (commit_batch).  Parsing
+// reads only the compiled rules, so it may run on another thread while the
+// context reduces.
+}  // namespace
+
+struct inet_parsed {
+  std::vector<FlatNet> fns;
+  std::vector<int> rcs;
+  std::vector<std::string> errs;
+  std::vector<uint8_t> taken;   // loaded into a context already
+  uint64_t rules_gen = 0;       // the rule set it was parsed with
+};
+
+namespace {
+
+void parse_batch(const CompiledRules& rules, uint64_t rules_gen, const char* buf, const uint64_t* offsets, int32_t n,
+                 inet_parsed& pb) {
+  pb.fns.assign((size_t)n, FlatNet());
+  pb.rcs.assign((size_t)n, 0);
+  pb.errs.assign((size_t)n, std::string());
+  pb.taken.assign((size_t)n, 0);
+  pb.rules_gen = rules_gen;
+  // body(lo, hi) over [0, n) in ranges of 16 nets on the host pool
+  HostPool::get().run(n, 16, [&](int32_t lo, int32_t hi) {
+    for (int32_t i = lo; i < hi; i++)
+      pb.rcs[(size_t)i] = flatten_net(std::string(buf + offsets[i], offsets[i + 1] - offsets[i]), rules, 0, 0, 0,
+                                      pb.fns[(size_t)i], pb.errs[(size_t)i]);
+  });
+}
+
+// Places nets [first, first + n) of a parsed batch: in order, ids first
+// (released ones, then never-used ones); the first net that failed to parse
+// or does not fit ends the batch, the nets before it stay loaded.  Each
+// net's indices are shifted to its place and its net id written into its
+// agent records, on the host pool, and the result appended to the staging
+// vectors.
+inet_status commit_batch(inet_ctx* ctx, inet_parsed& pb, int32_t first, int32_t n, int32_t* ids_out,
+                         int32_t* n_loaded_out) {
+  *n_loaded_out = 0;
+  if (!ctx->host_only) {
+    DeviceGuard g(ctx->device);
+    inet_status s = ensure_workspace(ctx);
+    if (s) return s;
+  }
+  std::vector<int32_t> pid((size_t)n);
+  for (int32_t i = 0; i < n; i++) pid[(size_t)i] = peek_net_id(ctx, (size_t)i);
+  FlatNet* fns = pb.fns.data() + first;
+  const int* rcs = pb.rcs.data() + first;
+  const std::string* errs = pb.errs.data() + first;
+  auto on_threads = [](int32_t cnt, const HostPool::Body& body) { HostPool::get().run(cnt, 16, body); };
+  std::vector<uint64_t> a_at((size_t)n + 1), v_at((size_t)n + 1);
+  a_at[0] = ctx->a_bump;
+  v_at[0] = ctx->v_bump;
+  int32_t m = 0;
+  inet_status stop = INET_OK;
+  std::string stop_msg;
+  for (; m < n; m++) {
+    const FlatNet& fn = fns[(size_t)m];
+    if (rcs[(size_t)m]) {
+      stop = (inet_status)rcs[(size_t)m];
+      stop_msg = errs[(size_t)m];
+      break;
+    }
+    if (pid[(size_t)m] < 0) {
+      stop = INET_ERR_ARENA_FULL;
+      stop_msg = "no free net slot";
+      break;
+    }
+    if (a_at[(size_t)m] + fn.nodes.size() > ctx->cfg.max_agents || v_at[(size_t)m] + fn.vars.size() > ctx->cfg.max_vars) {
+      stop = INET_ERR_ARENA_FULL;
+      stop_msg = "net does not fit the arena";
+      break;
+    }
+    a_at[(size_t)m + 1] = a_at[(size_t)m] + fn.nodes.size();
+    v_at[(size_t)m + 1] = v_at[(size_t)m] + fn.vars.size();
+  }
+  if (m > 0) {
+    if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
+      ctx->st_a0 = ctx->a_bump;
+      ctx->st_v0 = ctx->v_bump;
+    }
+    // staged entries continue the staging vectors: slot a_at[i] is entry
+    // a_at[i] - st_a0 (likewise for names)
+    const size_t na0 = ctx->st_nodes.size(), nv0 = ctx->st_vars.size();
+    ctx->st_nodes.resize(na0 + (size_t)(a_at[(size_t)m] - a_at[0]));
+    ctx->st_vars.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
+    ctx->st_vown.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
+    Node* dn = ctx->st_nodes.data() + na0;
+    uint32_t* dv = ctx->st_vars.data() + nv0;
+    uint32_t* downer = ctx->st_vown.data() + nv0;
+    on_threads(m, [&](int32_t lo, int32_t hi) {
+      for (int32_t i = lo; i < hi; i++) {
+        FlatNet& fn = fns[(size_t)i];
+        const uint32_t ab = (uint32_t)a_at[(size_t)i], vb = (uint32_t)v_at[(size_t)i];
+        auto shift = [ab, vb](uint32_t w) -> uint32_t {
+          return is_agent(w) ? mk_agent(idx_of(w) + ab) : is_var(w) ? mk_var(idx_of(w) + vb) : w;
+        };
+        const int32_t head_net = pid[(size_t)i] << 8;
+        Node* o = dn + (a_at[(size_t)i] - a_at[0]);
+        for (const Node& nd : fn.nodes) {
+          Node x = nd;
+          x.head = (x.head & 0xFF) | head_net;
+          for (uint32_t& w : x.aux) w = shift(w);
+          *o++ = x;
+        }
+        uint32_t* ov = dv + (v_at[(size_t)i] - v_at[0]);
+        for (uint32_t w : fn.vars) *ov++ = shift(w);
+        std::fill_n(downer + (v_at[(size_t)i] - v_at[0]), fn.vars.size(), (uint32_t)pid[(size_t)i]);
+        for (uint32_t& w : fn.iface) w = shift(w);
+        for (Pair& p : fn.pairs) {
+          p.a += ab;
+          p.b += ab;
+        }
+      }
+    });
+    ctx->a_bump = a_at[(size_t)m];
+    ctx->v_bump = v_at[(size_t)m];
+    ctx->live += (int64_t)(a_at[(size_t)m] - a_at[0]);
+    ctx->st_netctr.reserve(ctx->st_netctr.size() + (size_t)m);
+    ctx->st_net_ids.reserve(ctx->st_net_ids.size() + (size_t)m);
+    ctx->nets.reserve(ctx->nets.size() + (size_t)m);
+    for (int32_t i = 0; i < m; i++) {
+      FlatNet& fn = fns[(size_t)i];
+      const unsigned long long ctr = (unsigned long long)fn.pairs.size() << kNetPairShift;
+      NetRec nr;
+      nr.used = true;
+      nr.iface = std::move(fn.iface);
+      nr.pairs = std::move(fn.pairs);
+      commit_net(ctx, pid[(size_t)i], std::move(nr), ctr, (long long)fn.nodes.size());
+      ids_out[i] = pid[(size_t)i];
+      pb.taken[(size_t)(first + i)] = 1;
+    }
+    ctx->snap_valid = false;
+    ctx->arena_gen++;
+    *n_loaded_out = m;
+  }
+  if (stop) return fail(ctx, stop, stop_msg);
+  return INET_OK;
+}
+
 // Device buffers of one control run, freed on every exit.
 struct CtlBufs {
   std::vector<void*> p;
@@ -977,6 +1119,7 @@ inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len) {
   if (rc) return fail(ctx, rc, err);
   ctx->rules = std::move(r);
   ctx->have_rules = true;
+  ctx->rules_gen++;
   ctx->txt_labels_ok = false;
   if (ctx->host_only) return INET_OK;
   DeviceGuard g(ctx->device);
@@ -1060,116 +1203,50 @@ inet_status inet_load_nets(inet_ctx* ctx, const char* buf, const uint64_t* offse
   if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
   for (int32_t i = 0; i < n; i++)
     if (offsets[i + 1] < offsets[i]) return INET_ERR_INVALID_ARG;
-  if (!ctx->host_only) {
-    DeviceGuard g(ctx->device);
-    inet_status s = ensure_workspace(ctx);
-    if (s) return s;
-  }
-  // parse every net on its own (indices from 0) on a few host threads;
-  // then, in order, find how many nets load (the first error or the first
-  // net that does not fit ends the batch, the nets before it stay loaded);
-  // then the same threads shift each net's indices to its place and copy it
-  // into the staging vectors
-  // ids: released ones first, then never-used ones (-1: out of net slots)
-  std::vector<int32_t> pid((size_t)n);
-  for (int32_t i = 0; i < n; i++) pid[(size_t)i] = peek_net_id(ctx, (size_t)i);
-  std::vector<FlatNet> fns((size_t)n);
-  std::vector<int> rcs((size_t)n, 0);
-  std::vector<std::string> errs((size_t)n);
-  // body(lo, hi) over [0, cnt) in ranges of 16 nets on the host pool
-  auto on_threads = [](int32_t cnt, const HostPool::Body& body) { HostPool::get().run(cnt, 16, body); };
-  on_threads(n, [&](int32_t lo, int32_t hi) {
-    for (int32_t i = lo; i < hi; i++)
-      if (pid[(size_t)i] >= 0)
-        rcs[(size_t)i] = flatten_net(std::string(buf + offsets[i], offsets[i + 1] - offsets[i]), ctx->rules,
-                                     (uint32_t)pid[(size_t)i], 0, 0, fns[(size_t)i], errs[(size_t)i]);
-  });
-  std::vector<uint64_t> a_at((size_t)n + 1), v_at((size_t)n + 1);
-  a_at[0] = ctx->a_bump;
-  v_at[0] = ctx->v_bump;
-  int32_t m = 0;
-  inet_status stop = INET_OK;
-  std::string stop_msg;
-  for (; m < n; m++) {
-    const FlatNet& fn = fns[(size_t)m];
-    if (rcs[(size_t)m]) {
-      stop = (inet_status)rcs[(size_t)m];
-      stop_msg = errs[(size_t)m];
-      break;
-    }
-    if (pid[(size_t)m] < 0) {
-      stop = INET_ERR_ARENA_FULL;
-      stop_msg = "no free net slot";
-      break;
-    }
-    if (a_at[(size_t)m] + fn.nodes.size() > ctx->cfg.max_agents || v_at[(size_t)m] + fn.vars.size() > ctx->cfg.max_vars) {
-      stop = INET_ERR_ARENA_FULL;
-      stop_msg = "net does not fit the arena";
-      break;
-    }
-    a_at[(size_t)m + 1] = a_at[(size_t)m] + fn.nodes.size();
-    v_at[(size_t)m + 1] = v_at[(size_t)m] + fn.vars.size();
-  }
-  if (m > 0) {
-    if (ctx->st_nodes.empty() && ctx->st_vars.empty() && ctx->st_netctr.empty()) {
-      ctx->st_a0 = ctx->a_bump;
-      ctx->st_v0 = ctx->v_bump;
-    }
-    // staged entries continue the staging vectors: slot a_at[i] is entry
-    // a_at[i] - st_a0 (likewise for names)
-    const size_t na0 = ctx->st_nodes.size(), nv0 = ctx->st_vars.size();
-    ctx->st_nodes.resize(na0 + (size_t)(a_at[(size_t)m] - a_at[0]));
-    ctx->st_vars.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
-    ctx->st_vown.resize(nv0 + (size_t)(v_at[(size_t)m] - v_at[0]));
-    Node* dn = ctx->st_nodes.data() + na0;
-    uint32_t* dv = ctx->st_vars.data() + nv0;
-    uint32_t* downer = ctx->st_vown.data() + nv0;
-    on_threads(m, [&](int32_t lo, int32_t hi) {
-      for (int32_t i = lo; i < hi; i++) {
-        FlatNet& fn = fns[(size_t)i];
-        const uint32_t ab = (uint32_t)a_at[(size_t)i], vb = (uint32_t)v_at[(size_t)i];
-        auto shift = [ab, vb](uint32_t w) -> uint32_t {
-          return is_agent(w) ? mk_agent(idx_of(w) + ab) : is_var(w) ? mk_var(idx_of(w) + vb) : w;
-        };
-        Node* o = dn + (a_at[(size_t)i] - a_at[0]);
-        for (const Node& nd : fn.nodes) {
-          Node x = nd;
-          for (uint32_t& w : x.aux) w = shift(w);
-          *o++ = x;
-        }
-        uint32_t* ov = dv + (v_at[(size_t)i] - v_at[0]);
-        for (uint32_t w : fn.vars) *ov++ = shift(w);
-        std::fill_n(downer + (v_at[(size_t)i] - v_at[0]), fn.vars.size(), (uint32_t)pid[(size_t)i]);
-        for (uint32_t& w : fn.iface) w = shift(w);
-        for (Pair& p : fn.pairs) {
-          p.a += ab;
-          p.b += ab;
-        }
-      }
-    });
-    ctx->a_bump = a_at[(size_t)m];
-    ctx->v_bump = v_at[(size_t)m];
-    ctx->live += (int64_t)(a_at[(size_t)m] - a_at[0]);
-    ctx->st_netctr.reserve(ctx->st_netctr.size() + (size_t)m);
-    ctx->st_net_ids.reserve(ctx->st_net_ids.size() + (size_t)m);
-    ctx->nets.reserve(ctx->nets.size() + (size_t)m);
-    for (int32_t i = 0; i < m; i++) {
-      FlatNet& fn = fns[(size_t)i];
-      const unsigned long long ctr = (unsigned long long)fn.pairs.size() << kNetPairShift;
-      NetRec nr;
-      nr.used = true;
-      nr.iface = std::move(fn.iface);
-      nr.pairs = std::move(fn.pairs);
-      commit_net(ctx, pid[(size_t)i], std::move(nr), ctr, (long long)fn.nodes.size());
-      ids_out[i] = pid[(size_t)i];
-    }
-    ctx->snap_valid = false;
-    ctx->arena_gen++;
-    *n_loaded_out = m;
-  }
-  if (stop) return fail(ctx, stop, stop_msg);
+  inet_parsed pb;
+  parse_batch(ctx->rules, ctx->rules_gen, buf, offsets, n, pb);
+  return commit_batch(ctx, pb, 0, n, ids_out, n_loaded_out);
+}
+
+inet_status inet_parse_nets(const inet_ctx* ctx, const char* buf, const uint64_t* offsets, int32_t n,
+                            inet_parsed** out) {
+  if (!ctx || !out || n < 0 || (n > 0 && (!buf || !offsets))) return INET_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctx->have_rules) return INET_ERR_STATE;
+  for (int32_t i = 0; i < n; i++)
+    if (offsets[i + 1] < offsets[i]) return INET_ERR_INVALID_ARG;
+  inet_parsed* pb = new inet_parsed();
+  parse_batch(ctx->rules, ctx->rules_gen, buf, offsets, n, *pb);
+  *out = pb;
   return INET_OK;
 }
+
+inet_status inet_parsed_info(const inet_parsed* p, int32_t* n_out, uint64_t* agents_out) {
+  if (!p) return INET_ERR_INVALID_ARG;
+  if (n_out) *n_out = (int32_t)p->fns.size();
+  if (agents_out) {
+    uint64_t a = 0;
+    for (const FlatNet& fn : p->fns) a += fn.nodes.size();
+    *agents_out = a;
+  }
+  return INET_OK;
+}
+
+inet_status inet_load_parsed(inet_ctx* ctx, inet_parsed* p, int32_t first, int32_t n, int32_t* ids_out,
+                             int32_t* n_loaded_out) {
+  if (!ctx || !p || !n_loaded_out || first < 0 || n < 0 || (n > 0 && !ids_out) ||
+      (uint64_t)first + (uint64_t)n > p->fns.size())
+    return INET_ERR_INVALID_ARG;
+  *n_loaded_out = 0;
+  if (!ctx->have_rules) return fail(ctx, INET_ERR_STATE, "load rules first");
+  if (ctx->poisoned) return fail(ctx, INET_ERR_STATE, "context needs inet_reset after a fatal error");
+  if (p->rules_gen != ctx->rules_gen) return fail(ctx, INET_ERR_STATE, "parsed under another rule set");
+  for (int32_t i = first; i < first + n; i++)
+    if (p->taken[(size_t)i]) return fail(ctx, INET_ERR_INVALID_ARG, "net of the parsed batch already loaded");
+  return commit_batch(ctx, *p, first, n, ids_out, n_loaded_out);
+}
+
+void inet_parsed_free(inet_parsed* p) { delete p; }
 
 inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const inet_reduce_opts* opts,
                         inet_reduce_stats* stats) {

@@ -235,12 +235,55 @@ class Server:
     def busy(self) -> bool:
         return bool(self.inflight)
 
+    def _admit_parsed(self, chunk, now: float) -> int:
+        """Admits requests of a parsed chunk from chunk["next"] on, in order,
+        while they fit.  Returns how many."""
+        take, needs = 0, []
+        extra = 0
+        reqs = chunk["reqs"]
+        while chunk["next"] + take < len(reqs):
+            rid, text, size, arrival = reqs[chunk["next"] + take]
+            need = self.footprint(text, size)
+            if need > self.max_agents:
+                raise ValueError(f"request {rid} needs about {need} agent slots; the arena holds {self.max_agents}")
+            fits = (self.used + extra + need <= self.max_agents and
+                    len(self.inflight) + len(self.to_free) + take < self.max_nets)
+            if not fits and self.to_free:
+                self._free()
+                fits = (self.used + extra + need <= self.max_agents and
+                        len(self.inflight) + len(self.to_free) + take < self.max_nets)
+            if not fits:
+                break
+            needs.append(need)
+            extra += need
+            take += 1
+        if not take:
+            return 0
+        t0 = time.perf_counter()
+        nids = self.ev.load_parsed(chunk["parsed"], chunk["next"], take)
+        if self.quotas:
+            self.ev.set_quotas(nids, needs)
+        self.host_s["load"] += time.perf_counter() - t0
+        for (rid, _, _, arrival), need, nid in zip(reqs[chunk["next"]:chunk["next"] + take], needs, nids):
+            self.unstaged.append(nid)
+            self.used += need
+            self.inflight[nid] = (rid, arrival, now, need)
+            self.running += 1
+        chunk["next"] += take
+        return take
+
     def serve(self, requests, time_scale: float = 1.0, max_wall_s: float = math.inf,
               on_queue_empty=None) -> list[Finished]:
         """Runs `requests` (objects with .arrival_s, .net, .size) to the end.
         Arrivals are replayed on the wall clock, scaled by time_scale.
         on_queue_empty(t, done), if given, is called once, the first time
-        every request has arrived and been admitted."""
+        every request has arrived and been admitted.
+
+        The texts of arrived requests are built and parsed on a second host
+        thread (inet_parse_nets reads only the rule set), in chunks, while
+        this thread runs the device epochs; admission then only places
+        parsed nets (inet_load_parsed)."""
+        import threading
         reqs = sorted(enumerate(requests), key=lambda ir: ir[1].arrival_s)
         pending = collections.deque(reqs)
         t0 = time.perf_counter()
@@ -249,29 +292,81 @@ class Server:
             return time.perf_counter() - t0
 
         out: list[Finished] = []
-        waiting = collections.deque()   # (rid, request, text); texts are built when first tried
-        while pending or waiting or self.busy():
-            t = now()
-            if t > max_wall_s:
-                break
-            while pending and pending[0][1].arrival_s * time_scale <= t:
-                rid, r = pending.popleft()
-                waiting.append([rid, r, None])
-            if waiting:
-                batch = []
-                for w in itertools.islice(waiting, 4096):
-                    if w[2] is None:
-                        w[2] = w[1].net
-                    batch.append((w[0], w[2], w[1].size, w[1].arrival_s * time_scale))
-                for _ in range(self.admit_many(batch, now())):
-                    waiting.popleft()
-            if on_queue_empty is not None and not pending and not waiting:
-                on_queue_empty(now(), list(out))
-                on_queue_empty = None
-            if self.busy():
-                out.extend(self.epoch(now))
-            elif pending and not waiting:
-                time.sleep(max(0.0, min(0.001, pending[0][1].arrival_s * time_scale - now())))
+        to_parse = collections.deque()   # (rid, request) arrived, not yet parsed
+        parsed = collections.deque()     # chunks: {"reqs": [(rid, text, size, arrival)], "parsed", "next"}
+        lock = threading.Lock()
+        wake = threading.Event()
+        stop = threading.Event()
+        err = []
+        ahead = [0]                      # requests parsed and not yet admitted
+
+        def parser():
+            try:
+                while not stop.is_set():
+                    with lock:
+                        room = ahead[0] < 65536
+                        batch, nbytes = [], 0
+                        while room and to_parse and len(batch) < 2048 and nbytes < (8 << 20):
+                            rid, r = to_parse.popleft()
+                            batch.append((rid, r))
+                            nbytes += r.size
+                    if not batch:
+                        wake.wait(0.0005)
+                        wake.clear()
+                        continue
+                    rows = [(rid, r.net, r.size, r.arrival_s * time_scale) for rid, r in batch]
+                    p = self.ev.parse([t for _, t, _, _ in rows])
+                    with lock:
+                        parsed.append({"reqs": rows, "parsed": p, "next": 0})
+                        ahead[0] += len(rows)
+            except BaseException as e:  # surfaced on the serving thread
+                err.append(e)
+
+        th = threading.Thread(target=parser, daemon=True)
+        th.start()
+        try:
+            while pending or to_parse or parsed or ahead[0] or self.busy():
+                if err:
+                    raise err[0]
+                t = now()
+                if t > max_wall_s:
+                    break
+                arrived = False
+                while pending and pending[0][1].arrival_s * time_scale <= t:
+                    with lock:
+                        to_parse.append(pending.popleft())
+                    arrived = True
+                if arrived:
+                    wake.set()
+                while True:
+                    with lock:
+                        chunk = parsed[0] if parsed else None
+                    if chunk is None:
+                        break
+                    k = self._admit_parsed(chunk, now())
+                    with lock:
+                        ahead[0] -= k
+                        if chunk["next"] == len(chunk["reqs"]):
+                            parsed.popleft()
+                    if chunk["next"] < len(chunk["reqs"]):
+                        break                    # the next request does not fit yet
+                    wake.set()
+                if on_queue_empty is not None and not pending:
+                    with lock:
+                        empty = not to_parse and not parsed and ahead[0] == 0
+                    if empty:
+                        on_queue_empty(now(), list(out))
+                        on_queue_empty = None
+                if self.busy():
+                    out.extend(self.epoch(now))
+                elif pending and not to_parse and not parsed:
+                    time.sleep(max(0.0, min(0.001, pending[0][1].arrival_s * time_scale - now())))
+                else:
+                    time.sleep(50e-6)            # arrivals are being parsed
+        finally:
+            stop.set()
+            wake.set()
+            th.join()
         if self.to_free:
             self._free()
         return out

@@ -213,6 +213,44 @@ def test_batch_load_matches_one_by_one(capi):
     assert a == b
 
 
+def test_parsed_batches_load_like_load_nets(capi):
+    import threading
+    nets = W.config1(count=200).nets + [W.fib_net(7), "< a, b | Dup(a, b) = S(S(Z)) >", "< r | r = Z >"]
+    one, two = host_ctx(capi), host_ctx(capi)
+    for c in (one, two):
+        capi.inet_load_rules(c, W.ARITH_RULES)
+    ids1 = capi.inet_load_nets(one, nets)
+    # parsed on another thread, loaded in three slices
+    box = {}
+    th = threading.Thread(target=lambda: box.setdefault("p", capi.inet_parse_nets(two, nets)))
+    th.start()
+    th.join()
+    p = box["p"]
+    assert capi.inet_parsed_info(p)[0] == len(nets)
+    ids2 = capi.inet_load_parsed(two, p, 0, 50) + capi.inet_load_parsed(two, p, 50, 100) + \
+        capi.inet_load_parsed(two, p, 150, len(nets) - 150)
+    assert ids1 == ids2
+    assert capi.inet_arena_usage(one) == capi.inet_arena_usage(two)
+    for i in ids1:
+        assert capi.inet_net_info(one, i)["pending_pairs"] == capi.inet_net_info(two, i)["pending_pairs"]
+    with pytest.raises(capi.InetError) as e:      # each net of a batch loads once
+        capi.inet_load_parsed(two, p, 10, 1)
+    assert e.value.name == "INVALID_ARG"
+    capi.inet_parsed_free(p)
+    # a parse error surfaces when the net is loaded; the nets before it load
+    q = capi.inet_parse_nets(one, [W.add_net(1, 1), "< r | Nope(r) = Z >", W.add_net(2, 2)])
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_load_parsed(one, q, 0, 3)
+    assert e.value.name == "PARSE"
+    # a batch parsed under another rule set is refused
+    capi.inet_reset(one)
+    capi.inet_load_rules(one, W.ARITH_RULES)
+    with pytest.raises(capi.InetError) as e:
+        capi.inet_load_parsed(one, q, 2, 1)
+    assert e.value.name == "STATE"
+    capi.inet_parsed_free(q)
+
+
 def test_batch_load_stops_at_the_first_bad_net(capi):
     ctx = host_ctx(capi)
     capi.inet_load_rules(ctx, W.ARITH_RULES)

@@ -53,6 +53,12 @@ class FakeEvaluator:
     def load_nets(self, texts):
         return [self.load_net(t) for t in texts]
 
+    def parse(self, texts):
+        return list(texts)
+
+    def load_parsed(self, parsed, first, n):
+        return [self.load_net(t) for t in parsed[first:first + n]]
+
     def set_quotas(self, ids, quotas):
         pass
 
