@@ -91,9 +91,7 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
 # and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "43d6aac3659d"): 5_938_176 + 7_772_416,
-               ("mul2048", "persistent", "43d6aac3659d"): 11_565_056 + 25_113_088,
-               ("lsys27", "persistent", "43d6aac3659d"): 4_351_744 + 3_778_560}
+NCU_TRAFFIC = {("mul2048", "async", "fb657581c6ed"): 5_837_568 + 8_362_240}
 
 
 def kernel_source_hash() -> str:
