@@ -386,7 +386,11 @@ def main():
                     help="nets of the batch (every k-th) reduced one per launch by the host-driven loop")
     ap.add_argument("--serve-epoch-us", type=int, default=250)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
+    ap.add_argument("--no-jit", action="store_true",
+                    help="asynchronous mode on the general kernel, not the one compiled for the rule set")
     args = ap.parse_args()
+    if args.no_jit:
+        os.environ["INET_JIT"] = "0"  # read by every context this process creates
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -609,6 +613,12 @@ def main():
         for rec in narrow.values():
             rec["frac_of_hw_floor"] = per_level / rec["ns_per_level"]
 
+    ji = ev.jit_info()
+    jit_note = {"rule_specialised": bool(ji["enabled"] and ji["state"] == 1 and opts["mode"] == "async"),
+                "jit_state": ji["state"], "jit_compile_ms": round(ji["compile_ms"], 1), "jit_source": ji["source"],
+                "jit_launches": ji["launches"], "jit_msg": ji["msg"],
+                "how": "asynchronous mode compiles k_async for the loaded rule set at its first launch (NVRTC, "
+                       "before the timed steps); warps whose lanes all reduce one rule run that rule's code"}
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_leg(args, local)
@@ -622,6 +632,7 @@ def main():
                            "block": opts["block"] or 256, "grid": opts["grid"] or "auto",
                            "launch_shape": "autotuned" if tuned else "given",
                            "l2": "flushed (256 MiB write) before every timed step",
+                           "kernel": jit_note,
                            "parallelism": f"independent batches, {world} rank(s)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "plain": plain, "serving": serving, "paper_com_control": control,

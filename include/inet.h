@@ -394,6 +394,40 @@ inet_status inet_trace(inet_ctx* ctx, int64_t* frontier, int64_t* live, size_t c
  * Clears a poisoned state. */
 inet_status inet_reset(inet_ctx* ctx);
 
+/* ---- Rule-specialised asynchronous kernel ----------------------------------
+ * INET_MODE_ASYNC interprets each rule's instantiation template (Sec. 2.2,
+ * ->int: the agents of the right-hand side, their ports, the equations left
+ * to ->com) from shared memory.  The rule set is fixed once loaded, so the
+ * library also compiles, at the first asynchronous reduce of a rule set,
+ * the same kernel with the templates as constants (NVRTC, with the device
+ * headers the library was built from; a few seconds, then kept for the
+ * process and cached on disk in $INET_JIT_CACHE, by default jit-cache beside
+ * the library).  A warp whose lanes all reduce one rule then runs that rule's
+ * own code, with no template reads and no scans; other warps run the general
+ * code.  Results are identical either way.  When NVRTC is missing or fails
+ * the general kernel runs and inet_jit_info says why.  On by default; the
+ * environment variable INET_JIT=0 turns it off for new contexts. */
+typedef struct inet_jit_info_t {
+  int32_t enabled;     /* 1: asynchronous reduces use the specialised kernel */
+  int32_t state;       /* for the loaded rules: 0 not built yet, 1 built, -1 failed */
+  int32_t source;      /* the last build: 1 compiled, 2 on-disk cache, 3 already in this process */
+  int32_t pad;
+  double compile_ms;   /* NVRTC time of the last build (0 when from a cache) */
+  uint64_t launches;   /* asynchronous launches of this context that used it */
+  char msg[256];       /* why the last build failed ("" otherwise) */
+} inet_jit_info_t;
+
+/* Turns the specialised kernel on (1) or off (0) for this context. */
+inet_status inet_set_jit(inet_ctx* ctx, int32_t enable);
+/* State of the specialised kernel of this context. */
+inet_status inet_jit_info(const inet_ctx* ctx, inet_jit_info_t* out);
+/* Builds the specialised kernel for the loaded rules now (owner tracking:
+ * track = 1) instead of at the first asynchronous reduce.  On a host-only
+ * context (device < 0) it only compiles (or finds the cached cubin), which
+ * needs no GPU.  INET_ERR_STATE without rules, INET_ERR_CUDA (message in
+ * inet_last_error) when the build fails. */
+inet_status inet_jit_build(inet_ctx* ctx, int32_t track);
+
 /* Microbenchmark of the linker's primitive (->com, Sec. 2.2): random 32-bit
  * atomic exchanges that return the old value, over an array of n_slots
  * slots (allocated and freed here) on CUDA device `device`; about n_ops

@@ -64,10 +64,12 @@ class Evaluator:
     The workspace is one uint8 tensor from PyTorch's caching allocator and
     the context runs on PyTorch's current stream of that device.
     free_nets=True keeps the owner of every name slot, so that finished nets
-    can be freed (free()); it costs one store per name a reduction creates."""
+    can be freed (free()); it costs one store per name a reduction creates.
+    jit=False keeps the asynchronous mode on the general kernel instead of
+    the one compiled for the loaded rules (None: the library's default)."""
 
     def __init__(self, device: int = 0, max_agents: int = 0, max_vars: int = 0, max_pairs: int = 0,
-                 max_nets: int = 0, use_torch: bool = True, free_nets: bool = False):
+                 max_nets: int = 0, use_torch: bool = True, free_nets: bool = False, jit: bool | None = None):
         from . import capi
         self.cfg = capi.inet_arena_cfg(max_agents, max_vars, max_pairs, max_nets,
                                        capi.INET_ARENA_FREE_NETS if free_nets else 0)
@@ -78,6 +80,8 @@ class Evaluator:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         self.ctx = capi.inet_create(device, stream, self.cfg)
+        if jit is not None:
+            capi.inet_set_jit(self.ctx, jit)
         if device >= 0 and use_torch:
             import torch
             nbytes = capi.inet_workspace_bytes(self.cfg)
@@ -187,6 +191,14 @@ class Evaluator:
     def readback_counts(self) -> tuple[int, int]:
         """Texts inet_readback rendered on the device and on the host."""
         return capi_lazy.inet_readback_counts(self.ctx)
+
+    def jit_info(self) -> dict:
+        """State of the rule-specialised asynchronous kernel (inet_jit_info)."""
+        return capi_lazy.inet_jit_info(self.ctx)
+
+    def build_jit(self, track: bool = False) -> None:
+        """Builds the rule-specialised kernel now (inet_jit_build)."""
+        capi_lazy.inet_jit_build(self.ctx, track)
 
     def arena_usage(self) -> dict:
         """Bump pointers (agent and name slots handed out) and live agents."""

@@ -48,7 +48,7 @@ EXPORTED = [
     "inet_control_link", "inet_control_segsum", "inet_net_finished", "inet_load_nets",
     "inet_free_nets", "inet_free_net", "inet_arena_usage", "inet_bench_chase", "inet_readback_counts",
     "inet_set_quotas", "inet_net_status", "inet_parse_nets", "inet_parsed_info", "inet_load_parsed",
-    "inet_parsed_free",
+    "inet_parsed_free", "inet_set_jit", "inet_jit_info", "inet_jit_build",
 ]
 
 READ_CHUNK = 65536  # nets per non-blocking readback batch
@@ -88,6 +88,11 @@ class inet_arena_usage_t(C.Structure):
                 ("free_net_ids", C.c_uint32)]
 
 
+class inet_jit_info_t(C.Structure):
+    _fields_ = [("enabled", C.c_int32), ("state", C.c_int32), ("source", C.c_int32), ("pad", C.c_int32),
+                ("compile_ms", C.c_double), ("launches", C.c_uint64), ("msg", C.c_char * 256)]
+
+
 class InetError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -122,6 +127,9 @@ def _load():
         "inet_net_status": ([P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)], C.c_int32),
         "inet_readback_counts": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_arena_usage": ([P, C.POINTER(inet_arena_usage_t)], C.c_int32),
+        "inet_set_jit": ([P, C.c_int32], C.c_int32),
+        "inet_jit_info": ([P, C.POINTER(inet_jit_info_t)], C.c_int32),
+        "inet_jit_build": ([P, C.c_int32], C.c_int32),
         "inet_transfer_bytes": ([P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
         "inet_readback": ([P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int32),
         "inet_readback_nat": ([P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int32),
@@ -305,6 +313,22 @@ def inet_arena_usage(ctx) -> dict:
     u = inet_arena_usage_t()
     _check(ctx, LIB.inet_arena_usage(ctx, C.byref(u)))
     return {k: getattr(u, k) for k, _ in u._fields_}
+
+
+def inet_set_jit(ctx, enable: bool) -> None:
+    _check(ctx, LIB.inet_set_jit(ctx, 1 if enable else 0))
+
+
+def inet_jit_info(ctx) -> dict:
+    u = inet_jit_info_t()
+    _check(ctx, LIB.inet_jit_info(ctx, C.byref(u)))
+    d = {k: getattr(u, k) for k, _ in u._fields_ if k not in ("pad", "msg")}
+    d["msg"] = u.msg.decode(errors="replace")
+    return d
+
+
+def inet_jit_build(ctx, track: bool = False) -> None:
+    _check(ctx, LIB.inet_jit_build(ctx, 1 if track else 0))
 
 
 def inet_transfer_bytes(ctx) -> tuple[int, int]:

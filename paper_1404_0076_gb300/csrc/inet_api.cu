@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <thread>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -18,6 +20,7 @@
 #include "inet_micro.cuh"
 #include "inet_control.cuh"
 #include "inet_free.cuh"
+#include "inet_jit.h"
 #include "inet_paper.cuh"
 #include "inet_readback.cuh"
 #include "inet_textdev.cuh"
@@ -127,6 +130,15 @@ struct inet_ctx {
   bool have_rules = false;
   CompiledRules rules;
   uint64_t rules_gen = 0;                   // counts rule sets loaded
+  // rule-specialised asynchronous kernel (inet_jit.h): per owner tracking
+  // (0: without, 1: with) for the loaded rules
+  bool jit_on = true;
+  int jit_state[2] = {0, 0};                // 0: not built yet, 1: built, -1: failed
+  const void* jit_fn[2] = {nullptr, nullptr};
+  double jit_ms = 0;                        // NVRTC time of the last build (0 from a cache)
+  int jit_source = 0;                       // where the last build came from: 1 compiled, 2 disk, 3 process
+  uint64_t jit_launches = 0;                // asynchronous launches that used it
+  std::string jit_msg;
   // host mirrors of device counters
   uint64_t a_bump = 0, v_bump = 0;
   int64_t live = 0;
@@ -237,6 +249,23 @@ cudaError_t raise_smem(int which, const void* func, size_t bytes) {
   return e;
 }
 
+// The same for kernels loaded at run time (the rule-specialised ones): a
+// map by kernel and device.
+std::mutex g_smem_dyn_mu;
+std::map<std::pair<const void*, int>, size_t> g_smem_dyn;
+
+cudaError_t raise_smem_dyn(const void* func, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_smem_dyn_mu);
+  size_t& cur = g_smem_dyn[{func, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 // The loop kernels a context launches: the instantiations that keep name
 // owners and free marks when it was created with INET_ARENA_FREE_NETS.
 using KernelFn = void (*)(Dev);
@@ -252,6 +281,33 @@ LoopKernels loop_kernels(bool track) {
 inet_status fail(inet_ctx* c, inet_status code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
+}
+
+// The rule-specialised k_async (owner tracking: track) for the loaded rules,
+// built on first use and kept; null when turned off or when it cannot be
+// built (the general kernel then runs, and inet_jit_info says why).
+const void* jit_kernel(inet_ctx* ctx, int track) {
+  if (!ctx->jit_on || ctx->rules.tmpl.empty()) return nullptr;
+  if (ctx->jit_state[track] == 1) return ctx->jit_fn[track];
+  if (ctx->jit_state[track] == -1) return nullptr;
+  int ma = 0, mi = 0;
+  cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, ctx->device);
+  cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  char arch[32];
+  snprintf(arch, sizeof arch, "sm_%d%da", ma, mi);
+  JitResult jr;
+  std::string err;
+  if (!jit_async(ctx->rules.tmpl.data(), ctx->rules.tmpl.size(), track != 0, arch, true, &jr, &err)) {
+    ctx->jit_state[track] = -1;
+    ctx->jit_msg = err;
+    return nullptr;
+  }
+  ctx->jit_state[track] = 1;
+  ctx->jit_fn[track] = jr.fn;
+  ctx->jit_ms = jr.compile_ms;
+  ctx->jit_source = jr.from_memory ? 3 : (jr.from_disk ? 2 : 1);
+  ctx->jit_msg.clear();
+  return jr.fn;
 }
 
 #define CK(call)                                                                          \
@@ -308,6 +364,7 @@ void fill_dev(inet_ctx* ctx) {
   d.max_nets = ctx->cfg.max_nets;
   d.n_labels = (uint32_t)ctx->rules.n_labels();
   d.n_tmpl = (uint32_t)ctx->rules.tmpl.size();
+  d.rules_key = rules_key(ctx->rules.tmpl.data(), ctx->rules.tmpl.size());
   d.timeout_ns = kDefaultTimeoutNs;
   d.slice_ns = kSliceNs;
   d.solo_max = 0;
@@ -1044,6 +1101,7 @@ inet_status inet_create(inet_ctx** out, int device, void* stream, const inet_are
   ctx->lay = layout_of(c);
   ctx->device = device;
   ctx->host_only = device < 0;
+  if (const char* e = getenv("INET_JIT")) ctx->jit_on = strcmp(e, "0") != 0;
   if (!ctx->host_only) {
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
@@ -1121,10 +1179,52 @@ inet_status inet_load_rules(inet_ctx* ctx, const char* text, size_t len) {
   ctx->have_rules = true;
   ctx->rules_gen++;
   ctx->txt_labels_ok = false;
+  ctx->jit_state[0] = ctx->jit_state[1] = 0;
+  ctx->jit_fn[0] = ctx->jit_fn[1] = nullptr;
+  ctx->jit_msg.clear();
   if (ctx->host_only) return INET_OK;
   DeviceGuard g(ctx->device);
   drop_graph(ctx);
   return upload_rules(ctx);
+}
+
+inet_status inet_set_jit(inet_ctx* ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return INET_ERR_INVALID_ARG;
+  ctx->jit_on = enable != 0;
+  return INET_OK;
+}
+
+inet_status inet_jit_info(const inet_ctx* ctx, inet_jit_info_t* out) {
+  if (!ctx || !out) return INET_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  const int track = (ctx->cfg.flags & INET_ARENA_FREE_NETS) ? 1 : 0;
+  out->enabled = ctx->jit_on ? 1 : 0;
+  out->state = ctx->jit_state[track];
+  out->source = ctx->jit_source;
+  out->compile_ms = ctx->jit_ms;
+  out->launches = ctx->jit_launches;
+  snprintf(out->msg, sizeof out->msg, "%s", ctx->jit_msg.c_str());
+  return INET_OK;
+}
+
+inet_status inet_jit_build(inet_ctx* ctx, int32_t track) {
+  if (!ctx || (track != 0 && track != 1)) return INET_ERR_INVALID_ARG;
+  if (!ctx->have_rules || ctx->rules.tmpl.empty()) return fail(ctx, INET_ERR_STATE, "no rules loaded");
+  if (ctx->host_only) {
+    JitResult jr;
+    std::string err;
+    if (!jit_async(ctx->rules.tmpl.data(), ctx->rules.tmpl.size(), track != 0, "sm_103a", false, &jr, &err))
+      return fail(ctx, INET_ERR_CUDA, err);
+    ctx->jit_ms = jr.compile_ms;
+    ctx->jit_source = jr.from_memory ? 3 : (jr.from_disk ? 2 : 1);
+    return INET_OK;
+  }
+  DeviceGuard g(ctx->device);
+  const bool was_on = ctx->jit_on;
+  ctx->jit_on = true;
+  const void* f = jit_kernel(ctx, track);
+  ctx->jit_on = was_on;
+  return f ? INET_OK : fail(ctx, INET_ERR_CUDA, ctx->jit_msg);
 }
 
 inet_status inet_rule_count(const inet_ctx* ctx, int32_t* n_out) {
@@ -1307,9 +1407,13 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
   bool async_paused = false;
   if (fc[cur] > 0 && o.mode == INET_MODE_ASYNC) {
     const size_t smem_a = async_smem_bytes((uint32_t)B, d.n_labels, d.n_tmpl);
-    CK(raise_smem(kSmemAsync + K.track, (const void*)K.async, smem_a));
+    // the kernel specialised for the rule set when it can be had
+    const void* jf = jit_kernel(ctx, K.track);
+    const void* afn = jf ? jf : (const void*)K.async;
+    if (jf) CK(raise_smem_dyn(afn, smem_a));
+    else CK(raise_smem(kSmemAsync + K.track, afn, smem_a));
     int per = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K.async, B, smem_a));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, afn, B, smem_a));
     const int maxg = std::max(1, per) * ctx->num_sms;
     // default: one block per SM (more warps mostly add idle polling)
     const int grid = o.grid > 0 ? std::min(o.grid, maxg) : maxg;
@@ -1322,8 +1426,8 @@ inet_status inet_reduce(inet_ctx* ctx, const int32_t* net_ids, int32_t n, const 
       k_async_fill<<<fill_blocks, 256, 0, ctx->stream>>>(d);
       k_async_prep<<<1, 1, 0, ctx->stream>>>(d);
       void* args[] = {&d};
-      CK(cudaLaunchCooperativeKernel((const void*)K.async, dim3((unsigned)grid), dim3((unsigned)B), args, smem_a,
-                                     ctx->stream));
+      CK(cudaLaunchCooperativeKernel(afn, dim3((unsigned)grid), dim3((unsigned)B), args, smem_a, ctx->stream));
+      if (jf) ctx->jit_launches++;
       k_async_post<<<1, 1, 0, ctx->stream>>>(d);
       CK(cudaGetLastError());
       launches += 4;

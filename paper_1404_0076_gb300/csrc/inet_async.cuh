@@ -78,6 +78,21 @@ __device__ __forceinline__ void st_release64(unsigned long long* p, unsigned lon
 // ticket + 1; both compare all 64 bits, so no lap can be mistaken for
 // another however far ahead tickets were claimed.
 
+// A second arrival at name slot x: the slot is finished (its owner mark
+// cleared) and goes to the warp's staging list, or the ring when that is full.
+template <bool kTrack>
+__device__ __forceinline__ void release_name(const Dev& d, WarpMem& W, uint32_t x) {
+  __stcg(d.var + x, kEmpty);
+  if constexpr (kTrack) __stcg(d.vown + x, kNoNet);
+  const int pos = atomicAdd(&W.vstage_n, 1);
+  if (pos < kVStageW) {
+    W.vstage[pos] = x;
+  } else {
+    const unsigned long long tp = atomicAdd(&d.ctrl->v_tail, 1ull);
+    __stcg(d.vfree + tp % d.cap_vars, x);
+  }
+}
+
 // ->com for the asynchronous kernel (the chase after a second arrival):
 // link_eq with freed name slots staged per warp.  The lane has fenced its
 // new records before linking; a lane that receives a reference through an
@@ -103,15 +118,7 @@ __device__ __forceinline__ bool link_async(const Dev& d, WarpMem& W, uint32_t t,
     const uint32_t x = idx_of(t);
     const uint32_t old = atomicExch(d.var + x, u);
     if (old == kEmpty) return false;
-    __stcg(d.var + x, kEmpty);
-    if constexpr (kTrack) __stcg(d.vown + x, kNoNet);
-    const int pos = atomicAdd(&W.vstage_n, 1);
-    if (pos < kVStageW) {
-      W.vstage[pos] = x;
-    } else {
-      const unsigned long long tp = atomicAdd(&d.ctrl->v_tail, 1ull);
-      __stcg(d.vfree + tp % d.cap_vars, x);
-    }
+    release_name<kTrack>(d, W, x);
     t = old;
   }
 }
@@ -149,11 +156,310 @@ struct WarpStacks {
   int ac, vc;
 };
 
+// Where one warp step's new slots come from (warp-uniform): this warp's
+// stacks first (ta agent and tv name slots from abase / vbase up); when a
+// stack runs dry, one global pop serves the rest of the step (ga, gv slots)
+// and refills the stack with kRefill more (gra, grv).
+struct PopPlan {
+  uint32_t ta, tv, abase, vbase, ga, gv, gra, grv;
+  unsigned long long arb, abb, vrb, vbb;
+  uint32_t aav, vav;
+};
+
+// Plans the pops of Ka agent and Kv name slots (warp-collective).  Returns
+// false when the arena is full (fatal: the loop stops).
+__device__ __forceinline__ bool warp_pop(const Dev& d, const WarpStacks& S, uint32_t Ka, uint32_t Kv, int lane,
+                                         PopPlan& P) {
+  Ctrl* c = d.ctrl;
+  P.ta = min((uint32_t)S.ac, Ka);
+  P.tv = min((uint32_t)S.vc, Kv);
+  P.abase = (uint32_t)S.ac - P.ta;
+  P.vbase = (uint32_t)S.vc - P.tv;
+  P.ga = Ka - P.ta;
+  P.gv = Kv - P.tv;
+  P.gra = P.ga ? (uint32_t)kRefill : 0u;
+  P.grv = P.gv ? (uint32_t)kRefill : 0u;
+  P.arb = P.abb = P.vrb = P.vbb = 0;
+  P.aav = P.vav = 0;
+  if (P.ga | P.gv) {
+    uint32_t ok = 1;
+    if (lane == 0) {
+      ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, P.ga + P.gra, &P.arb, &P.aav, &P.abb) ? 1u : 0u;
+      ok &= pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, P.gv + P.grv, &P.vrb, &P.vav, &P.vbb) ? 1u : 0u;
+      if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
+    }
+    if (!__shfl_sync(kFull, ok, 0)) return false;
+    P.arb = __shfl_sync(kFull, P.arb, 0);
+    P.abb = __shfl_sync(kFull, P.abb, 0);
+    P.aav = __shfl_sync(kFull, P.aav, 0);
+    P.vrb = __shfl_sync(kFull, P.vrb, 0);
+    P.vbb = __shfl_sync(kFull, P.vbb, 0);
+    P.vav = __shfl_sync(kFull, P.vav, 0);
+  }
+  return true;
+}
+
+// The k-th agent / name slot of this warp step.
+__device__ __forceinline__ uint32_t plan_agent(const Dev& d, const WarpMem& W, const PopPlan& P, uint32_t k) {
+  return k < P.ta ? W.astk[P.abase + k] : pool_slot(d.afree, d.cap_agents, P.arb, P.aav, P.abb, k - P.ta);
+}
+__device__ __forceinline__ uint32_t plan_var(const Dev& d, const WarpMem& W, const PopPlan& P, uint32_t k) {
+  return k < P.tv ? W.vstk[P.vbase + k] : pool_slot(d.vfree, d.cap_vars, P.vrb, P.vav, P.vbb, k - P.tv);
+}
+
+// After every lane has read its stack entries (warp-collective): the
+// refills of the stacks, then the agent slots this step frees (free_a of
+// this lane, Fa of the warp; the lane's first at offset `of`) on top of the
+// agent stack, the overflow to the ring.
+template <bool kTrack>
+__device__ __forceinline__ void warp_settle(const Dev& d, WarpMem& W, WarpStacks& S, const PopPlan& P, uint32_t Fa,
+                                            uint32_t free_a, uint32_t of, bool first_is_a, uint32_t a, uint32_t b,
+                                            int lane) {
+  Ctrl* c = d.ctrl;
+  if (P.gra | P.grv) {
+    if ((uint32_t)lane < P.gra) W.astk[P.abase + lane] = pool_slot(d.afree, d.cap_agents, P.arb, P.aav, P.abb, P.ga + lane);
+    if ((uint32_t)lane < P.grv) W.vstk[P.vbase + lane] = pool_slot(d.vfree, d.cap_vars, P.vrb, P.vav, P.vbb, P.gv + lane);
+  }
+  const uint32_t atop = P.abase + P.gra;
+  const uint32_t keep = min((uint32_t)kAStack - atop, Fa);
+  if (Fa) {
+    unsigned long long over = 0;
+    if (Fa > keep) {
+      if (lane == 0) over = atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep));
+      over = __shfl_sync(kFull, over, 0);
+    }
+    for (uint32_t f = 0; f < free_a; f++) {
+      const uint32_t slot = (first_is_a && f == 0) ? a : b;
+      const uint32_t k = of + f;
+      if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
+      if (k < keep) W.astk[atop + k] = slot;
+      else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
+    }
+  }
+  S.ac = (int)(atop + keep);
+  S.vc = (int)(P.vbase + P.grv);
+}
+
+// Names freed while linking (warp-collective): on the warp's stack, the
+// overflow to the ring.
+__device__ __forceinline__ void flush_vstage(const Dev& d, WarpMem& W, WarpStacks& S, int lane) {
+  __syncwarp();
+  const int nst = W.vstage_n;
+  if (nst) {
+    const int nv = min(nst, kVStageW);
+    const int keepv = min(kVStack - S.vc, nv);
+    unsigned long long over = 0;
+    if (lane == 0 && nv > keepv) over = atomicAdd(&d.ctrl->v_tail, (unsigned long long)(nv - keepv));
+    over = __shfl_sync(kFull, over, 0);
+    for (int j = lane; j < nv; j += 32) {
+      if (j < keepv) W.vstk[S.vc + j] = W.vstage[j];
+      else __stcg(d.vfree + (over + (unsigned long long)(j - keepv)) % d.cap_vars, W.vstage[j]);
+    }
+    S.vc += keepv;
+    __syncwarp();
+    if (lane == 0) W.vstage_n = 0;
+    __syncwarp();
+  }
+}
+
+// Per-net counters (interactions and the change of pending pairs) and the
+// rule histogram: one fire-and-forget atomic each; with kTrack the net's
+// live agents too (its quota is checked between launches).
+template <bool kTrack>
+__device__ __forceinline__ void count_interaction(const Dev& d, uint32_t* hist, uint32_t net, uint32_t rule,
+                                                  uint32_t np, uint32_t n_new) {
+  atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)np - 1) << kNetPairShift));
+  atomicAdd(&hist[rule], 1u);
+  if constexpr (kTrack) {
+    if (n_new != 2) atomicAdd(reinterpret_cast<unsigned long long*>(d.netlive + net),
+                              (unsigned long long)((long long)n_new - 2));
+  }
+}
+
+// ->com of one lane's equations t_k = u_k, k < nl, after its new records
+// (per lane, no warp-collective step).  One fence makes this lane's new
+// records and fresh names visible before an exchange can publish a
+// reference to them; the first exchange of each of the first kBatch
+// equations is then issued back to back, and only second arrivals continue
+// (rarely) with a chase.  get(k, 0) and get(k, 1) are the two sides of
+// equation k.  kNL >= 0: nl is that constant (the loops unroll); -1: nl is
+// known at run time.  The new active pairs go to W.out[0..return)[lane].
+template <bool kTrack, int kNL, class Get>
+__device__ __forceinline__ uint32_t link_lane(const Dev& d, WarpMem& W, uint32_t nl, const Get& get, int lane) {
+  if constexpr (kNL >= 0) nl = (uint32_t)kNL;
+  constexpr uint32_t kBatch = 2;
+  uint32_t np = 0;
+  __threadfence();
+  uint32_t lt[kBatch], lu[kBatch], lo[kBatch];
+#pragma unroll
+  for (uint32_t k = 0; k < kBatch; k++) {
+    lt[k] = 0;
+    lu[k] = 0;
+    lo[k] = kEmpty;
+    if (k < nl) {
+      uint32_t t = get(k, 0), u = get(k, 1);
+      if (!(is_agent(t) && is_agent(u))) {
+        if (!is_var(t)) {
+          const uint32_t w = t;
+          t = u;
+          u = w;
+        }
+        if (is_var(t) && idx_of(t) < d.cap_vars) lo[k] = atomicExch(d.var + idx_of(t), u);
+        else set_error(d.ctrl, INET_ERR_STATE, 1);
+      }
+      lt[k] = t;
+      lu[k] = u;
+    }
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kBatch; k++) {
+    if (k < nl) {
+      const uint32_t t = lt[k], u = lu[k];
+      if (is_agent(t) && is_agent(u)) {
+        W.out[np][lane] = Pair{idx_of(t), idx_of(u)};
+        np++;
+      } else if (lo[k] != kEmpty && is_var(t)) {
+        // second arrival: the slot is finished; continue with old = u
+        release_name<kTrack>(d, W, idx_of(t));
+        Pair out;
+        if (link_async<kTrack>(d, W, lo[k], u, &out)) {
+          W.out[np][lane] = out;
+          np++;
+        }
+      }
+    }
+  }
+  if constexpr (kNL >= 0) {
+#pragma unroll
+    for (uint32_t k = kBatch; k < (uint32_t)kNL; k++) {
+      Pair out;
+      if (link_async<kTrack>(d, W, get(k, 0), get(k, 1), &out)) {
+        W.out[np][lane] = out;
+        np++;
+      }
+    }
+  } else {
+    for (uint32_t k = kBatch; k < nl; k++) {
+      Pair out;
+      if (link_async<kTrack>(d, W, get(k, 0), get(k, 1), &out)) {
+        W.out[np][lane] = out;
+        np++;
+      }
+    }
+  }
+  return np;
+}
+
+// The rule set a kernel is specialised for: kN templates known at compile
+// time (kT, in rule-table order) and kKey, the hash of their bytes the host
+// passes in Dev::rules_key.  NoRules (kN = 0): the general kernel, which
+// reads the templates from shared memory.
+struct NoRules {
+  static constexpr int kN = 0;
+  static constexpr unsigned long long kKey = 0;
+  static constexpr Template kT[1] = {};
+};
+
+// Instantiation of rule I of a specialised rule set for one lane (Sec. 2.2,
+// ->int, then ->com of Theta'): the template is a constant, so the values
+// live in registers and every loop over agents, ports, names and equations
+// is unrolled.  Slots come from the warp's plan at the lane's offsets oa
+// (agents beyond the two reused ones) and ov (fresh names).
+template <bool kTrack, class Rules, int I>
+__device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const PopPlan& P, const int4& ra,
+                                              const int4& rb, uint32_t a, uint32_t b, uint32_t net, uint32_t oa,
+                                              uint32_t ov, int lane, bool& valid) {
+  constexpr Template R = Rules::kT[I];
+  uint32_t v[kNumVals];
+  v[kValExt + 0] = (uint32_t)ra.y;
+  v[kValExt + 1] = (uint32_t)ra.z;
+  v[kValExt + 2] = (uint32_t)ra.w;
+  v[kValExt + 3] = (uint32_t)rb.y;
+  v[kValExt + 4] = (uint32_t)rb.z;
+  v[kValExt + 5] = (uint32_t)rb.w;
+#pragma unroll
+  for (int j = kValNew; j < kNumVals; j++) v[j] = 0;
+  bool in_range = true;
+  if (R.n_new > 0) v[kValNew + 0] = mk_agent(a);
+  if (R.n_new > 1) v[kValNew + 1] = mk_agent(b);
+#pragma unroll
+  for (int j = 2; j < (int)R.n_new; j++) {
+    const uint32_t sl = plan_agent(d, W, P, oa + (uint32_t)j - 2);
+    if (sl >= d.cap_agents) in_range = false;
+    v[kValNew + j] = mk_agent(sl);
+  }
+#pragma unroll
+  for (int f = 0; f < (int)R.n_fresh; f++) {
+    const uint32_t x = plan_var(d, W, P, ov + (uint32_t)f);
+    if (x >= d.cap_vars) {
+      in_range = false;
+    } else {
+      __stcg(d.var + x, kEmpty);  // a fresh name starts empty; published by this lane's fence
+      if constexpr (kTrack) __stcg(d.vown + x, net);
+    }
+    v[kValFresh + f] = mk_var(x);
+  }
+  if (!in_range) {
+    set_error(d.ctrl, INET_ERR_STATE, 4);
+    valid = false;
+    return 0u;
+  }
+  const uint32_t head_net = net << 8;
+#pragma unroll
+  for (int j = 0; j < (int)R.n_new; j++) {
+    int4 rec;
+    rec.x = (int32_t)(head_net | R.lab[j]);
+    rec.y = R.src[j][0] == kValNone ? 0 : (int32_t)v[R.src[j][0]];
+    rec.z = R.src[j][1] == kValNone ? 0 : (int32_t)v[R.src[j][1]];
+    rec.w = R.src[j][2] == kValNone ? 0 : (int32_t)v[R.src[j][2]];
+    st_node(d.node + idx_of(v[kValNew + j]), rec);
+  }
+  if (R.n_link == 0) return 0u;
+  return link_lane<kTrack, R.n_link>(d, W, R.n_link, [&](uint32_t k, int s) { return v[R.link[k][s]]; }, lane);
+}
+
+// A warp whose valid lanes all reduce rule I of a specialised rule set (the
+// common case: one lane alone on a chain, or a batch of like pairs): the
+// whole step with that rule's template as a constant.  Every lane needs the
+// same slots, so a lane's offsets among the warp's needs are its rank among
+// the valid lanes times the rule's counts, with no scan.
+template <bool kTrack, class Rules, int I>
+__device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
+                                                 unsigned vmask, uint32_t a, uint32_t b, const int4& ra,
+                                                 const int4& rb, uint32_t net, long long& live) {
+  constexpr Template R = Rules::kT[I];
+  constexpr uint32_t NN = R.n_new, NF = R.n_fresh;
+  constexpr uint32_t NA = NN > 2 ? NN - 2 : 0u, FA = NN < 2 ? 2 - NN : 0u;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nvl = __popc(vmask), rank = __popc(vmask & lanemask_lt());
+  const uint32_t Ka = nvl * NA, Kv = nvl * NF, Fa = nvl * FA;
+  PopPlan P;
+  if (!warp_pop(d, S, Ka, Kv, lane, P)) return 0u;
+  if (lane == 0) live += (long long)Ka - (long long)Fa;
+  const uint32_t free_a = valid ? FA : 0u;  // counted in Fa, so freed even if the step fails below
+  uint32_t np = 0;
+  if (valid) np = rule_body<kTrack, Rules, I>(d, W, P, ra, rb, a, b, net, rank * NA, rank * NF, lane, valid);
+  __syncwarp();  // every taken stack entry has been read
+  warp_settle<kTrack>(d, W, S, P, Fa, free_a, rank * FA, NN == 0, a, b, lane);
+  flush_vstage(d, W, S, lane);
+  if (valid) count_interaction<kTrack>(d, hist, net, R.rule, np, NN);
+  return valid ? np : 0u;
+}
+
+// Rule I of a specialised rule set, when the rule set has one.
+#define INET_UNI_CASE(I)                                                                                   \
+  case I:                                                                                                  \
+    if constexpr (I < Rules::kN) return uni_interact<kTrack, Rules, I>(d, hist, W, S, valid, vmask, a, b, ra, rb, net, live); \
+    break;
+
 // One interaction per lane whose `valid` is set (warp-collective).  The new
 // active pairs are left in W.out[0..return)[lane]; a pair that cannot be
 // reduced (no rule, corrupt state) is dropped and returns 0.  Lane 0's
-// `live` collects the change of live agents.
-template <bool kTrack>
+// `live` collects the change of live agents.  With a specialised rule set,
+// a warp whose lanes all reduce the same rule takes that rule's own code;
+// any other warp (and the general kernel always) interprets the templates
+// in shared memory.
+template <bool kTrack, class Rules>
 __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl* tmpl, const int16_t* tab,
                                                    uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
                                                    uint32_t a, uint32_t b, long long& live, bool pre,
@@ -193,6 +499,27 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
       ti = (uint32_t)e >> 1;
     }
   }
+  if constexpr (Rules::kN > 0) {
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    const uint32_t lead = __shfl_sync(kFull, ti, vmask ? __ffs(vmask) - 1 : 0);
+    if (vmask && __all_sync(kFull, !valid || ti == lead)) {
+      switch (lead) {
+        INET_UNI_CASE(0) INET_UNI_CASE(1) INET_UNI_CASE(2) INET_UNI_CASE(3) INET_UNI_CASE(4) INET_UNI_CASE(5)
+        INET_UNI_CASE(6) INET_UNI_CASE(7) INET_UNI_CASE(8) INET_UNI_CASE(9) INET_UNI_CASE(10) INET_UNI_CASE(11)
+        INET_UNI_CASE(12) INET_UNI_CASE(13) INET_UNI_CASE(14) INET_UNI_CASE(15) INET_UNI_CASE(16) INET_UNI_CASE(17)
+        INET_UNI_CASE(18) INET_UNI_CASE(19) INET_UNI_CASE(20) INET_UNI_CASE(21) INET_UNI_CASE(22) INET_UNI_CASE(23)
+        INET_UNI_CASE(24) INET_UNI_CASE(25) INET_UNI_CASE(26) INET_UNI_CASE(27) INET_UNI_CASE(28) INET_UNI_CASE(29)
+        INET_UNI_CASE(30) INET_UNI_CASE(31) INET_UNI_CASE(32) INET_UNI_CASE(33) INET_UNI_CASE(34) INET_UNI_CASE(35)
+        INET_UNI_CASE(36) INET_UNI_CASE(37) INET_UNI_CASE(38) INET_UNI_CASE(39) INET_UNI_CASE(40) INET_UNI_CASE(41)
+        INET_UNI_CASE(42) INET_UNI_CASE(43) INET_UNI_CASE(44) INET_UNI_CASE(45) INET_UNI_CASE(46) INET_UNI_CASE(47)
+        INET_UNI_CASE(48) INET_UNI_CASE(49) INET_UNI_CASE(50) INET_UNI_CASE(51) INET_UNI_CASE(52) INET_UNI_CASE(53)
+        INET_UNI_CASE(54) INET_UNI_CASE(55) INET_UNI_CASE(56) INET_UNI_CASE(57) INET_UNI_CASE(58) INET_UNI_CASE(59)
+        INET_UNI_CASE(60) INET_UNI_CASE(61) INET_UNI_CASE(62) INET_UNI_CASE(63)
+        default: break;
+      }
+    }
+  }
+  static_assert(INET_MAX_RULES == 64, "one case per rule");
   const AsyncTpl& T = tmpl[ti];
   const uint32_t hdr = valid ? T.hdr : 0u;
   const uint32_t n_new = hdr & 0xFFu, n_fresh = (hdr >> 8) & 0xFFu, n_link = (hdr >> 16) & 0xFFu;
@@ -210,29 +537,8 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
   const uint32_t tot = __shfl_sync(kFull, inc, 31), ex = inc - packed;
   const uint32_t Ka = tot & 1023u, Kv = (tot >> 10) & 1023u, Fa = tot >> 20;
   const uint32_t oa = ex & 1023u, ov = (ex >> 10) & 1023u, of = ex >> 20;
-  // the warp's stacks first; when one runs dry, one global pop serves this
-  // interaction and refills the stack with kRefill slots (warp-uniform)
-  const uint32_t ta = min((uint32_t)S.ac, Ka), tv = min((uint32_t)S.vc, Kv);
-  const uint32_t abase = (uint32_t)S.ac - ta, vbase = (uint32_t)S.vc - tv;
-  const uint32_t ga = Ka - ta, gv = Kv - tv;
-  const uint32_t gra = ga ? (uint32_t)kRefill : 0u, grv = gv ? (uint32_t)kRefill : 0u;
-  unsigned long long arb = 0, abb = 0, vrb = 0, vbb = 0;
-  uint32_t aav = 0, vav = 0;
-  if (ga | gv) {
-    uint32_t ok = 1;
-    if (lane == 0) {
-      ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &arb, &aav, &abb) ? 1u : 0u;
-      ok &= pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &vrb, &vav, &vbb) ? 1u : 0u;
-      if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
-    }
-    if (!__shfl_sync(kFull, ok, 0)) return 0u;  // fatal: the loop stops
-    arb = __shfl_sync(kFull, arb, 0);
-    abb = __shfl_sync(kFull, abb, 0);
-    aav = __shfl_sync(kFull, aav, 0);
-    vrb = __shfl_sync(kFull, vrb, 0);
-    vbb = __shfl_sync(kFull, vbb, 0);
-    vav = __shfl_sync(kFull, vav, 0);
-  }
+  PopPlan P;
+  if (!warp_pop(d, S, Ka, Kv, lane, P)) return 0u;
   if (lane == 0) live += (long long)Ka - (long long)Fa;
   if (valid) {
     W.vals[kValExt + 0][lane] = (uint32_t)ra.y;
@@ -245,14 +551,12 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
     if (n_new > 0) W.vals[kValNew + 0][lane] = mk_agent(a);
     if (n_new > 1) W.vals[kValNew + 1][lane] = mk_agent(b);
     for (uint32_t j = 2; j < n_new; j++) {
-      const uint32_t k = oa + j - 2;
-      const uint32_t sl = k < ta ? W.astk[abase + k] : pool_slot(d.afree, d.cap_agents, arb, aav, abb, k - ta);
+      const uint32_t sl = plan_agent(d, W, P, oa + j - 2);
       if (sl >= d.cap_agents) in_range = false;
       W.vals[kValNew + j][lane] = mk_agent(sl);
     }
     for (uint32_t v = 0; v < n_fresh; v++) {
-      const uint32_t k = ov + v;
-      const uint32_t x = k < tv ? W.vstk[vbase + k] : pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, k - tv);
+      const uint32_t x = plan_var(d, W, P, ov + v);
       if (x >= d.cap_vars) {
         in_range = false;
       } else {
@@ -267,32 +571,9 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
     }
   }
   __syncwarp();  // every taken stack entry has been read
-  // refills of the stacks, then this warp's agent frees on top (or the ring)
-  if (gra | grv) {
-    if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, arb, aav, abb, ga + lane);
-    if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, gv + lane);
-  }
-  const uint32_t atop = abase + gra;
-  const uint32_t keep = min((uint32_t)kAStack - atop, Fa);
-  if (Fa) {
-    unsigned long long over = 0;
-    if (Fa > keep) {
-      if (lane == 0) over = atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep));
-      over = __shfl_sync(kFull, over, 0);
-    }
-    if (free_a) {
-      for (uint32_t f = 0; f < free_a; f++) {
-        const uint32_t slot = (n_new == 0 && f == 0) ? a : b;
-        const uint32_t k = of + f;
-        if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
-        if (k < keep) W.astk[atop + k] = slot;
-        else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
-      }
-    }
-  }
-  S.ac = (int)(atop + keep);
-  S.vc = (int)(vbase + grv);
+  warp_settle<kTrack>(d, W, S, P, Fa, free_a, of, n_new == 0, a, b, lane);
   // a2: the new agents' records
+  uint32_t np = 0;
   if (valid) {
     const uint32_t head_net = net << 8;
     for (uint32_t j = 0; j < n_new; j++) {
@@ -304,105 +585,18 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
       rec.w = port_val(W, w >> 24, lane);
       st_node(d.node + idx_of(W.vals[kValNew + j][lane]), rec);
     }
-  }
-  // a4: link.  One fence makes this lane's new records and fresh names
-  // visible before an exchange can publish a reference to them; the first
-  // exchange of each of the first kBatch equations is then issued back to
-  // back, and only second arrivals continue (rarely) with a chase.
-  constexpr uint32_t kBatch = 2;
-  uint32_t np = 0;
-  const uint32_t nl = valid ? n_link : 0u;
-  if (__any_sync(kFull, nl != 0)) {
-    if (nl) __threadfence();
-    uint32_t lt[kBatch], lu[kBatch], lo[kBatch];
-#pragma unroll
-    for (uint32_t k = 0; k < kBatch; k++) {
-      lt[k] = 0;
-      lu[k] = 0;
-      lo[k] = kEmpty;
-      if (k < nl) {
+    // a4: link
+    if (n_link)
+      np = link_lane<kTrack, -1>(d, W, n_link, [&](uint32_t k, int s) {
         const uint32_t lk = T.link[k];
-        uint32_t t = W.vals[lk & 0xFFu][lane], u = W.vals[lk >> 8][lane];
-        if (!(is_agent(t) && is_agent(u))) {
-          if (!is_var(t)) {
-            const uint32_t w = t;
-            t = u;
-            u = w;
-          }
-          if (is_var(t) && idx_of(t) < d.cap_vars) lo[k] = atomicExch(d.var + idx_of(t), u);
-          else set_error(c, INET_ERR_STATE, 1);
-        }
-        lt[k] = t;
-        lu[k] = u;
-      }
-    }
-#pragma unroll
-    for (uint32_t k = 0; k < kBatch; k++) {
-      if (k < nl) {
-        const uint32_t t = lt[k], u = lu[k];
-        if (is_agent(t) && is_agent(u)) {
-          W.out[np][lane] = Pair{idx_of(t), idx_of(u)};
-          np++;
-        } else if (lo[k] != kEmpty && is_var(t)) {
-          // second arrival: the slot is finished; continue with old = u
-          const uint32_t x = idx_of(t);
-          __stcg(d.var + x, kEmpty);
-          if constexpr (kTrack) __stcg(d.vown + x, kNoNet);
-          const int pos = atomicAdd(&W.vstage_n, 1);
-          if (pos < kVStageW) {
-            W.vstage[pos] = x;
-          } else {
-            const unsigned long long tp = atomicAdd(&c->v_tail, 1ull);
-            __stcg(d.vfree + tp % d.cap_vars, x);
-          }
-          Pair out;
-          if (link_async<kTrack>(d, W, lo[k], u, &out)) {
-            W.out[np][lane] = out;
-            np++;
-          }
-        }
-      }
-    }
-    for (uint32_t k = kBatch; k < nl; k++) {
-      const uint32_t lk = T.link[k];
-      Pair out;
-      if (link_async<kTrack>(d, W, W.vals[lk & 0xFFu][lane], W.vals[lk >> 8][lane], &out)) {
-        W.out[np][lane] = out;
-        np++;
-      }
-    }
+        return W.vals[s ? lk >> 8 : lk & 0xFFu][lane];
+      }, lane);
   }
-  __syncwarp();
-  // names freed while linking: on the warp's stack, the overflow to the ring
-  const int nst = W.vstage_n;
-  if (nst) {
-    const int nv = min(nst, kVStageW);
-    const int keepv = min(kVStack - S.vc, nv);
-    unsigned long long over = 0;
-    if (lane == 0 && nv > keepv) over = atomicAdd(&c->v_tail, (unsigned long long)(nv - keepv));
-    over = __shfl_sync(kFull, over, 0);
-    for (int j = lane; j < nv; j += 32) {
-      if (j < keepv) W.vstk[S.vc + j] = W.vstage[j];
-      else __stcg(d.vfree + (over + (unsigned long long)(j - keepv)) % d.cap_vars, W.vstage[j]);
-    }
-    S.vc += keepv;
-    __syncwarp();
-    if (lane == 0) W.vstage_n = 0;
-    __syncwarp();
-  }
-  // per-net counters (interactions and the change of pending pairs) and the
-  // rule histogram: one fire-and-forget atomic each
-  if (valid) {
-    atomicAdd(d.netctr + net, 1ull + ((unsigned long long)((long long)np - 1) << kNetPairShift));
-    atomicAdd(&hist[hdr >> 24], 1u);
-    // live agents of the net (its quota is checked between launches)
-    if constexpr (kTrack) {
-      if (n_new != 2) atomicAdd(reinterpret_cast<unsigned long long*>(d.netlive + net),
-                                (unsigned long long)((long long)n_new - 2));
-    }
-  }
+  flush_vstage(d, W, S, lane);
+  if (valid) count_interaction<kTrack>(d, hist, net, hdr >> 24, np, n_new);
   return valid ? np : 0u;
 }
+#undef INET_UNI_CASE
 
 // Writes a pair back to the exit frontier (other buffer).
 __device__ __forceinline__ void exit_pair(const Dev& d, Pair p) {
@@ -452,8 +646,15 @@ __device__ __forceinline__ bool wait_ticket(const Dev& d, const Pair* Q, unsigne
   }
 }
 
-template <bool kTrack>
+template <bool kTrack, class Rules = NoRules>
 __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
+  if constexpr (Rules::kN > 0) {
+    // a specialised kernel runs only on the rule set it was built for
+    if (d.rules_key != Rules::kKey || d.n_tmpl != (uint32_t)Rules::kN) {
+      if (threadIdx.x == 0 && blockIdx.x == 0) set_error(d.ctrl, INET_ERR_STATE, 10);
+      return;
+    }
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t off = 0;
   auto take = [&](size_t n) { off = (off + 15) / 16 * 16; unsigned char* p = smem_raw + off; off += n; return p; };
@@ -568,7 +769,7 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
       continue;
     }
     nap = 0;
-    const uint32_t np = async_interact<kTrack>(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb);
+    const uint32_t np = async_interact<kTrack, Rules>(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb);
     // keep the first new pair and start loading its records now, so the
     // load overlaps the rest of this iteration
     const bool had = have;

@@ -116,6 +116,7 @@ struct Dev {
   int use_cond;
   uint32_t qcur;   // asynchronous kernel: frontier buffer used as the ticket queue
   uint32_t pad2;
+  unsigned long long rules_key;  // hash of the templates (a rule-specialised kernel checks it)
 };
 
 // ---------------------------------------------------------------------------
