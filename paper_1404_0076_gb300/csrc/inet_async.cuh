@@ -363,13 +363,20 @@ struct NoRules {
 // Instantiation of rule I of a specialised rule set for one lane (Sec. 2.2,
 // ->int, then ->com of Theta'): the template is a constant, so the values
 // live in registers and every loop over agents, ports, names and equations
-// is unrolled.  Slots come from the warp's plan at the lane's offsets oa
-// (agents beyond the two reused ones) and ov (fresh names).
+// is unrolled.  Slots: the lane's agents beyond the two it reuses start at
+// offset oa of the warp's step, its fresh names at ov (taken from the
+// warp's stacks below ta / tv, the rest from the global pops).  The linking
+// is written out here rather than shared with the general path: the
+// compiler then keeps each equation's known cases (a new agent is an agent,
+// a fresh name a name) apart.
 template <bool kTrack, class Rules, int I>
-__device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const PopPlan& P, const int4& ra,
-                                              const int4& rb, uint32_t a, uint32_t b, uint32_t net, uint32_t oa,
-                                              uint32_t ov, int lane, bool& valid) {
+__device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const int4& ra, const int4& rb, uint32_t a,
+                                              uint32_t b, uint32_t net, uint32_t oa, uint32_t ov, uint32_t ta,
+                                              uint32_t tv, uint32_t abase, uint32_t vbase, unsigned long long arb,
+                                              uint32_t aav, unsigned long long abb, unsigned long long vrb,
+                                              uint32_t vav, unsigned long long vbb, int lane, bool& valid) {
   constexpr Template R = Rules::kT[I];
+  Ctrl* c = d.ctrl;
   uint32_t v[kNumVals];
   v[kValExt + 0] = (uint32_t)ra.y;
   v[kValExt + 1] = (uint32_t)ra.z;
@@ -384,13 +391,15 @@ __device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const Po
   if (R.n_new > 1) v[kValNew + 1] = mk_agent(b);
 #pragma unroll
   for (int j = 2; j < (int)R.n_new; j++) {
-    const uint32_t sl = plan_agent(d, W, P, oa + (uint32_t)j - 2);
+    const uint32_t k = oa + (uint32_t)j - 2;
+    const uint32_t sl = k < ta ? W.astk[abase + k] : pool_slot(d.afree, d.cap_agents, arb, aav, abb, k - ta);
     if (sl >= d.cap_agents) in_range = false;
     v[kValNew + j] = mk_agent(sl);
   }
 #pragma unroll
   for (int f = 0; f < (int)R.n_fresh; f++) {
-    const uint32_t x = plan_var(d, W, P, ov + (uint32_t)f);
+    const uint32_t k = ov + (uint32_t)f;
+    const uint32_t x = k < tv ? W.vstk[vbase + k] : pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, k - tv);
     if (x >= d.cap_vars) {
       in_range = false;
     } else {
@@ -400,7 +409,7 @@ __device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const Po
     v[kValFresh + f] = mk_var(x);
   }
   if (!in_range) {
-    set_error(d.ctrl, INET_ERR_STATE, 4);
+    set_error(c, INET_ERR_STATE, 4);
     valid = false;
     return 0u;
   }
@@ -414,8 +423,58 @@ __device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const Po
     rec.w = R.src[j][2] == kValNone ? 0 : (int32_t)v[R.src[j][2]];
     st_node(d.node + idx_of(v[kValNew + j]), rec);
   }
-  if (R.n_link == 0) return 0u;
-  return link_lane<kTrack, R.n_link>(d, W, R.n_link, [&](uint32_t k, int s) { return v[R.link[k][s]]; }, lane);
+  // ->com: the fence, the first exchanges of the first kBatch equations back
+  // to back, then their second arrivals, then the other equations
+  constexpr uint32_t kBatch = 2;
+  uint32_t np = 0;
+  if (R.n_link) __threadfence();
+  uint32_t lt[kBatch], lu[kBatch], lo[kBatch];
+#pragma unroll
+  for (uint32_t k = 0; k < kBatch; k++) {
+    lt[k] = 0;
+    lu[k] = 0;
+    lo[k] = kEmpty;
+    if (k < R.n_link) {
+      uint32_t t = v[R.link[k][0]], u = v[R.link[k][1]];
+      if (!(is_agent(t) && is_agent(u))) {
+        if (!is_var(t)) {
+          const uint32_t w = t;
+          t = u;
+          u = w;
+        }
+        if (is_var(t) && idx_of(t) < d.cap_vars) lo[k] = atomicExch(d.var + idx_of(t), u);
+        else set_error(c, INET_ERR_STATE, 1);
+      }
+      lt[k] = t;
+      lu[k] = u;
+    }
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kBatch; k++) {
+    if (k < R.n_link) {
+      const uint32_t t = lt[k], u = lu[k];
+      if (is_agent(t) && is_agent(u)) {
+        W.out[np][lane] = Pair{idx_of(t), idx_of(u)};
+        np++;
+      } else if (lo[k] != kEmpty && is_var(t)) {
+        release_name<kTrack>(d, W, idx_of(t));
+        Pair out;
+        if (link_async<kTrack>(d, W, lo[k], u, &out)) {
+          W.out[np][lane] = out;
+          np++;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (uint32_t k = kBatch; k < R.n_link; k++) {
+    Pair out;
+    if (link_async<kTrack>(d, W, v[R.link[k][0]], v[R.link[k][1]], &out)) {
+      W.out[np][lane] = out;
+      np++;
+    }
+  }
+  return np;
 }
 
 // A warp whose valid lanes all reduce rule I of a specialised rule set (the
@@ -431,16 +490,63 @@ __device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, W
   constexpr uint32_t NN = R.n_new, NF = R.n_fresh;
   constexpr uint32_t NA = NN > 2 ? NN - 2 : 0u, FA = NN < 2 ? 2 - NN : 0u;
   const int lane = threadIdx.x & 31;
+  Ctrl* c = d.ctrl;
   const uint32_t nvl = __popc(vmask), rank = __popc(vmask & lanemask_lt());
   const uint32_t Ka = nvl * NA, Kv = nvl * NF, Fa = nvl * FA;
-  PopPlan P;
-  if (!warp_pop(d, S, Ka, Kv, lane, P)) return 0u;
+  const uint32_t oa = rank * NA, ov = rank * NF, of = rank * FA;
+  const uint32_t ta = min((uint32_t)S.ac, Ka), tv = min((uint32_t)S.vc, Kv);
+  const uint32_t abase = (uint32_t)S.ac - ta, vbase = (uint32_t)S.vc - tv;
+  const uint32_t ga = Ka - ta, gv = Kv - tv;
+  const uint32_t gra = ga ? (uint32_t)kRefill : 0u, grv = gv ? (uint32_t)kRefill : 0u;
+  unsigned long long arb = 0, abb = 0, vrb = 0, vbb = 0;
+  uint32_t aav = 0, vav = 0;
+  if (ga | gv) {
+    uint32_t ok = 1;
+    if (lane == 0) {
+      ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &arb, &aav, &abb) ? 1u : 0u;
+      ok &= pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &vrb, &vav, &vbb) ? 1u : 0u;
+      if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
+    }
+    if (!__shfl_sync(kFull, ok, 0)) return 0u;  // fatal: the loop stops
+    arb = __shfl_sync(kFull, arb, 0);
+    abb = __shfl_sync(kFull, abb, 0);
+    aav = __shfl_sync(kFull, aav, 0);
+    vrb = __shfl_sync(kFull, vrb, 0);
+    vbb = __shfl_sync(kFull, vbb, 0);
+    vav = __shfl_sync(kFull, vav, 0);
+  }
   if (lane == 0) live += (long long)Ka - (long long)Fa;
-  const uint32_t free_a = valid ? FA : 0u;  // counted in Fa, so freed even if the step fails below
+  const bool frees = valid;  // counted in Fa: freed even if the step fails below
   uint32_t np = 0;
-  if (valid) np = rule_body<kTrack, Rules, I>(d, W, P, ra, rb, a, b, net, rank * NA, rank * NF, lane, valid);
+  if (valid)
+    np = rule_body<kTrack, Rules, I>(d, W, ra, rb, a, b, net, oa, ov, ta, tv, abase, vbase, arb, aav, abb, vrb, vav,
+                                     vbb, lane, valid);
   __syncwarp();  // every taken stack entry has been read
-  warp_settle<kTrack>(d, W, S, P, Fa, free_a, rank * FA, NN == 0, a, b, lane);
+  if (gra | grv) {
+    if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, arb, aav, abb, ga + lane);
+    if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, gv + lane);
+  }
+  const uint32_t atop = abase + gra;
+  const uint32_t keep = min((uint32_t)kAStack - atop, Fa);
+  if (FA && Fa) {
+    unsigned long long over = 0;
+    if (Fa > keep) {
+      if (lane == 0) over = atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep));
+      over = __shfl_sync(kFull, over, 0);
+    }
+    if (frees) {
+#pragma unroll
+      for (uint32_t f = 0; f < FA; f++) {
+        const uint32_t slot = (NN == 0 && f == 0) ? a : b;
+        const uint32_t k = of + f;
+        if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
+        if (k < keep) W.astk[atop + k] = slot;
+        else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
+      }
+    }
+  }
+  S.ac = (int)(atop + keep);
+  S.vc = (int)(vbase + grv);
   flush_vstage(d, W, S, lane);
   if (valid) count_interaction<kTrack>(d, hist, net, R.rule, np, NN);
   return valid ? np : 0u;
@@ -648,13 +754,6 @@ __device__ __forceinline__ bool wait_ticket(const Dev& d, const Pair* Q, unsigne
 
 template <bool kTrack, class Rules = NoRules>
 __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
-  if constexpr (Rules::kN > 0) {
-    // a specialised kernel runs only on the rule set it was built for
-    if (d.rules_key != Rules::kKey || d.n_tmpl != (uint32_t)Rules::kN) {
-      if (threadIdx.x == 0 && blockIdx.x == 0) set_error(d.ctrl, INET_ERR_STATE, 10);
-      return;
-    }
-  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   size_t off = 0;
   auto take = [&](size_t n) { off = (off + 15) / 16 * 16; unsigned char* p = smem_raw + off; off += n; return p; };
@@ -665,6 +764,15 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
   for (uint32_t i = threadIdx.x; i < d.n_tmpl; i += blockDim.x) tmpl[i] = pack_template(d.tmpl[i]);
   for (uint32_t i = threadIdx.x; i < d.n_labels * d.n_labels; i += blockDim.x) tab[i] = d.table[i];
   for (uint32_t i = threadIdx.x; i < INET_MAX_RULES; i += blockDim.x) hist[i] = 0;
+  if constexpr (Rules::kN > 0) {
+    // a specialised kernel runs only on the rule set it was built for (the
+    // check sits after the carve-up of shared memory: at the top of the
+    // kernel it cost the loop 6 more registers)
+    if (d.rules_key != Rules::kKey || d.n_tmpl != (uint32_t)Rules::kN) {
+      if (threadIdx.x == 0 && blockIdx.x == 0) set_error(d.ctrl, INET_ERR_STATE, 10);
+      return;
+    }
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem& W = wm[wid];
   if (lane == 0) W.vstage_n = 0;
