@@ -402,7 +402,8 @@ inet_status inet_reset(inet_ctx* ctx);
  * the same kernel with the templates as constants (NVRTC, with the device
  * headers the library was built from; a few seconds, then kept for the
  * process and cached on disk in $INET_JIT_CACHE, by default jit-cache beside
- * the library).  A warp whose lanes all reduce one rule then runs that rule's
+ * the library).  A warp whose lanes all reduce one rule whose right-hand side
+ * has at most two agents (the rules that carry chains) then runs that rule's
  * own code, with no template reads and no scans; other warps run the general
  * code.  Results are identical either way.  When NVRTC is missing or fails
  * the general kernel runs and inet_jit_info says why.  On by default; the

@@ -552,10 +552,22 @@ __device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, W
   return valid ? np : 0u;
 }
 
-// Rule I of a specialised rule set, when the rule set has one.
+// Rule I of a specialised rule set, when the rule set has one and I's
+// right-hand side has at most two agents (it reuses the pair's two slots:
+// the rules that carry chains, Add(y, r) = S(x) and the like).  Larger
+// rules stay on the general code: their own copies cost more in instruction
+// fetch than they save (2048 Mul nets: 10.9 ms with rules of up to two
+// agents, 11.0 ms up to three, 11.2 ms with every rule; only up to one
+// leaves the Add chains out and gives no gain).
+template <class Rules, int I>
+__host__ __device__ constexpr bool specialised() {
+  if constexpr (I < Rules::kN) return Rules::kT[I].n_new <= 2;
+  return false;
+}
 #define INET_UNI_CASE(I)                                                                                   \
   case I:                                                                                                  \
-    if constexpr (I < Rules::kN) return uni_interact<kTrack, Rules, I>(d, hist, W, S, valid, vmask, a, b, ra, rb, net, live); \
+    if constexpr (specialised<Rules, I>())                                                                 \
+      return uni_interact<kTrack, Rules, I>(d, hist, W, S, valid, vmask, a, b, ra, rb, net, live);         \
     break;
 
 // One interaction per lane whose `valid` is set (warp-collective).  The new

@@ -4,12 +4,13 @@
 // agents of Theta, their ports and the equations of Theta') from shared
 // memory.  A rule set is fixed once loaded, so the same kernel can also be
 // compiled with the templates as constants (k_async<kTrack, Rules>): a warp
-// whose lanes all reduce one rule then runs that rule's straight-line code,
-// with the values in registers.  This unit generates that source for a rule
-// set, compiles it at run time with NVRTC (loaded with dlopen, so a missing
-// NVRTC only turns the specialisation off), loads the cubin and keeps it for
-// the process; cubins are also cached on disk, keyed by the templates, the
-// embedded kernel sources, the NVRTC version and the architecture.
+// whose lanes all reduce one rule of at most two right-hand-side agents then
+// runs that rule's straight-line code, with the values in registers.  This
+// unit generates that source for a rule set, compiles it at run time with
+// NVRTC (loaded with dlopen, so a missing NVRTC only turns the
+// specialisation off), loads the cubin and keeps it for the process; cubins
+// are also cached on disk, keyed by the templates, the embedded kernel
+// sources, the NVRTC version and the architecture.
 #pragma once
 
 #include <cstddef>
