@@ -90,8 +90,9 @@ def bytes_per_rule(rules: list[dict], batched: bool) -> list[int]:
 
 # DRAM bytes per launch from ncu captures (profiles/), valid only for the
 # kernel sources they were taken on (sha1 prefix over csrc/inet_kernels.cuh
-# and csrc/inet_async.cuh).
-NCU_TRAFFIC = {("mul2048", "async", "fb657581c6ed"): 5_837_568 + 8_362_240}
+# and csrc/inet_async.cuh) and for the kernel they were taken of (the last
+# key: the asynchronous kernel compiled for the rule set, or the general one).
+NCU_TRAFFIC = {}
 
 
 def kernel_source_hash() -> str:
@@ -459,12 +460,15 @@ def main():
     # k_persistent) or, for the step kernels, per reduction step
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / total_s / 1e9
-    traffic = NCU_TRAFFIC.get((args.workload, opts["mode"], kernel_source_hash()))
+    ji = ev.jit_info()
+    specialised = bool(ji["enabled"] and ji["state"] == 1 and opts["mode"] == "async")
+    traffic = NCU_TRAFFIC.get((args.workload, opts["mode"], kernel_source_hash(), specialised))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "bytes_per_interaction": alg_bytes / max(1, ints),
             # the same fraction at the DRAM bytes ncu measured for one launch
             "frac_at_traffic": (traffic / (total_s / args.steps) / 1e9) / peak if traffic else None,
-            "kernel": {"async": "k_async", "persistent": "k_persistent", "graph": "k_step", "plain": "k_step"}[opts["mode"]],
+            "kernel": {"async": "k_async" + ("<rule-specialised>" if specialised else ""), "persistent": "k_persistent",
+                       "graph": "k_step", "plain": "k_step"}[opts["mode"]],
             "launch_time": "device time of the reduce call (for async: the queue fill, set-up and wind-down "
                            "kernels around k_async add a few microseconds)"}
 
@@ -614,7 +618,7 @@ def main():
             rec["frac_of_hw_floor"] = per_level / rec["ns_per_level"]
 
     ji = ev.jit_info()
-    jit_note = {"rule_specialised": bool(ji["enabled"] and ji["state"] == 1 and opts["mode"] == "async"),
+    jit_note = {"rule_specialised": specialised,
                 "jit_state": ji["state"], "jit_compile_ms": round(ji["compile_ms"], 1), "jit_source": ji["source"],
                 "jit_launches": ji["launches"], "jit_msg": ji["msg"],
                 "how": "asynchronous mode compiles k_async for the loaded rule set at its first launch (NVRTC, "

@@ -559,10 +559,18 @@ __device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, W
 // fetch than they save (2048 Mul nets: 10.9 ms with rules of up to two
 // agents, 11.0 ms up to three, 11.2 ms with every rule; only up to one
 // leaves the Add chains out and gives no gain).
+constexpr int kSpecialisedMaxNew = 2;
+// Bit I set: rule I has its own code.
+template <class Rules>
+__host__ __device__ constexpr unsigned long long spec_mask() {
+  unsigned long long m = 0;
+  for (int i = 0; i < Rules::kN; i++)
+    if (Rules::kT[i].n_new <= kSpecialisedMaxNew) m |= 1ull << i;
+  return m;
+}
 template <class Rules, int I>
 __host__ __device__ constexpr bool specialised() {
-  if constexpr (I < Rules::kN) return Rules::kT[I].n_new <= 2;
-  return false;
+  return I < Rules::kN && ((spec_mask<Rules>() >> I) & 1ull);
 }
 #define INET_UNI_CASE(I)                                                                                   \
   case I:                                                                                                  \
@@ -620,7 +628,7 @@ __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl*
   if constexpr (Rules::kN > 0) {
     const unsigned vmask = __ballot_sync(kFull, valid);
     const uint32_t lead = __shfl_sync(kFull, ti, vmask ? __ffs(vmask) - 1 : 0);
-    if (vmask && __all_sync(kFull, !valid || ti == lead)) {
+    if (vmask && ((spec_mask<Rules>() >> lead) & 1ull) && __all_sync(kFull, !valid || ti == lead)) {
       switch (lead) {
         INET_UNI_CASE(0) INET_UNI_CASE(1) INET_UNI_CASE(2) INET_UNI_CASE(3) INET_UNI_CASE(4) INET_UNI_CASE(5)
         INET_UNI_CASE(6) INET_UNI_CASE(7) INET_UNI_CASE(8) INET_UNI_CASE(9) INET_UNI_CASE(10) INET_UNI_CASE(11)
