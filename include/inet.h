@@ -407,7 +407,8 @@ inet_status inet_reset(inet_ctx* ctx);
  * own code, with no template reads and no scans; other warps run the general
  * code.  Results are identical either way.  When NVRTC is missing or fails
  * the general kernel runs and inet_jit_info says why.  On by default; the
- * environment variable INET_JIT=0 turns it off for new contexts. */
+ * environment variable INET_JIT=0 turns it off for new contexts, and
+ * INET_NVRTC_LIB names the NVRTC library to open instead of searching. */
 typedef struct inet_jit_info_t {
   int32_t enabled;     /* 1: asynchronous reduces use the specialised kernel */
   int32_t state;       /* for the loaded rules: 0 not built yet, 1 built, -1 failed */

@@ -71,15 +71,20 @@ const Nvrtc& nvrtc() {
   static Nvrtc n;
   static std::once_flag once;
   std::call_once(once, [] {
+    // $INET_NVRTC_LIB names the library to use, and only it; otherwise the
+    // loader's search path, then the CUDA installation
     std::vector<std::string> cands;
-    if (const char* e = getenv("INET_NVRTC_LIB")) cands.push_back(e);
-    cands.push_back("libnvrtc.so.13");
-    cands.push_back("libnvrtc.so");
-    const char* homes[] = {getenv("CUDA_HOME"), getenv("CUDA_PATH"), "/usr/local/cuda"};
-    for (const char* home : homes) {
-      if (!home) continue;
-      cands.push_back(std::string(home) + "/lib64/libnvrtc.so.13");
-      cands.push_back(std::string(home) + "/lib64/libnvrtc.so");
+    if (const char* e = getenv("INET_NVRTC_LIB")) {
+      cands.push_back(e);
+    } else {
+      cands.push_back("libnvrtc.so.13");
+      cands.push_back("libnvrtc.so");
+      const char* homes[] = {getenv("CUDA_HOME"), getenv("CUDA_PATH"), "/usr/local/cuda"};
+      for (const char* home : homes) {
+        if (!home) continue;
+        cands.push_back(std::string(home) + "/lib64/libnvrtc.so.13");
+        cands.push_back(std::string(home) + "/lib64/libnvrtc.so");
+      }
     }
     void* h = nullptr;
     for (const std::string& c : cands)

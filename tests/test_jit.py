@@ -148,3 +148,33 @@ def test_jit_chain_and_slices():
     assert ev.readback_nat(i) == (20007, 20001)
     assert ev.jit_info()["launches"] >= 1
     ev.close()
+
+
+def test_jit_without_nvrtc_reports_why(tmp_path):
+    # a process whose NVRTC cannot be opened: the build fails with the
+    # reason, nothing is cached, and nothing else changes
+    code = ("from paper_1404_0076_gb300 import capi as C; import workloads as W; "
+            "ctx = C.inet_create(-1); C.inet_load_rules(ctx, W.ARITH_RULES)\n"
+            "try:\n    C.inet_jit_build(ctx, False)\nexcept C.InetError as e:\n    print(e.name, str(e))\n")
+    env = dict(os.environ, INET_NVRTC_LIB=str(tmp_path / "missing.so"), INET_JIT_CACHE=str(tmp_path))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120, env=env)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("CUDA") and "NVRTC" in out.stdout
+    assert not list(tmp_path.glob("*.cubin"))
+
+
+@pytest.mark.gpu
+def test_jit_missing_nvrtc_falls_back_to_the_general_kernel(tmp_path):
+    # the specialised kernel cannot be built: asynchronous reduces run on
+    # the general kernel with the same results, and the context says why
+    code = ("import torch, workloads as W\n"
+            "from paper_1404_0076_gb300 import Evaluator\n"
+            "ev = Evaluator(device=0, max_agents=1 << 20, max_vars=1 << 20, max_pairs=1 << 16, max_nets=64)\n"
+            "ev.load_rules(W.ARITH_RULES)\n"
+            "ids = ev.load_nets([W.mul_net(7, 9), W.add_net(300, 4)])\n"
+            "ev.reduce(ids, mode='async')\n"
+            "print(ev.readback_nats(ids)[0], ev.jit_info()['state'], ev.jit_info()['launches'], ev.jit_info()['msg'])\n")
+    env = dict(os.environ, INET_NVRTC_LIB=str(tmp_path / "missing.so"), INET_JIT_CACHE=str(tmp_path))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("[63, 304] -1 0 NVRTC"), out.stdout
