@@ -424,7 +424,8 @@ inet_status inet_set_jit(inet_ctx* ctx, int32_t enable);
 /* State of the specialised kernel of this context. */
 inet_status inet_jit_info(const inet_ctx* ctx, inet_jit_info_t* out);
 /* Builds the specialised kernel for the loaded rules now (owner tracking:
- * track = 1) instead of at the first asynchronous reduce.  On a host-only
+ * track = 1; -1: the instantiation this context launches) instead of at the
+ * first asynchronous reduce.  On a host-only
  * context (device < 0) it only compiles (or finds the cached cubin), which
  * needs no GPU.  INET_ERR_STATE without rules, INET_ERR_CUDA (message in
  * inet_last_error) when the build fails. */

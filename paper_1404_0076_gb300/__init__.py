@@ -196,8 +196,9 @@ class Evaluator:
         """State of the rule-specialised asynchronous kernel (inet_jit_info)."""
         return capi_lazy.inet_jit_info(self.ctx)
 
-    def build_jit(self, track: bool = False) -> None:
-        """Builds the rule-specialised kernel now (inet_jit_build)."""
+    def build_jit(self, track: bool | None = None) -> None:
+        """Builds the rule-specialised kernel now (inet_jit_build); by
+        default the instantiation this context launches."""
         capi_lazy.inet_jit_build(self.ctx, track)
 
     def arena_usage(self) -> dict:

@@ -327,8 +327,9 @@ def inet_jit_info(ctx) -> dict:
     return d
 
 
-def inet_jit_build(ctx, track: bool = False) -> None:
-    _check(ctx, LIB.inet_jit_build(ctx, 1 if track else 0))
+def inet_jit_build(ctx, track: bool | None = False) -> None:
+    """track None: the instantiation the context launches."""
+    _check(ctx, LIB.inet_jit_build(ctx, -1 if track is None else (1 if track else 0)))
 
 
 def inet_transfer_bytes(ctx) -> tuple[int, int]:

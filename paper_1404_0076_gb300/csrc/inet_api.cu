@@ -1208,7 +1208,8 @@ inet_status inet_jit_info(const inet_ctx* ctx, inet_jit_info_t* out) {
 }
 
 inet_status inet_jit_build(inet_ctx* ctx, int32_t track) {
-  if (!ctx || (track != 0 && track != 1)) return INET_ERR_INVALID_ARG;
+  if (!ctx || track < -1 || track > 1) return INET_ERR_INVALID_ARG;
+  if (track < 0) track = (ctx->cfg.flags & INET_ARENA_FREE_NETS) ? 1 : 0;
   if (!ctx->have_rules || ctx->rules.tmpl.empty()) return fail(ctx, INET_ERR_STATE, "no rules loaded");
   if (ctx->host_only) {
     JitResult jr;

@@ -72,6 +72,15 @@ class Server:
                                  max_pairs=max_pairs, max_nets=max_nets, free_nets=True)
         self.ev = make_evaluator()
         self.ev.load_rules(rules)
+        # the asynchronous kernel for these rules is compiled now, not in the
+        # first epoch a request waits for (without NVRTC the general kernel
+        # serves, and the build's error says why)
+        if hasattr(self.ev, "build_jit"):
+            from .capi import InetError
+            try:
+                self.ev.build_jit()
+            except InetError:
+                pass
         self.max_nets = max_nets
         self.epoch_us = epoch_us
         self.block, self.grid = block, grid
