@@ -89,11 +89,11 @@ def make_ev(**kw):
     return Evaluator(device=0, **kw)
 
 
-def run_async(nets, rules, jit, free_nets=False, **caps):
+def run_async(nets, rules, jit, free_nets=False, mode="async", **caps):
     ev = make_ev(jit=jit, free_nets=free_nets, **caps)
     ev.load_rules(rules)
     ids = ev.load_nets(nets)
-    st = ev.reduce(ids, mode="async")
+    st = ev.reduce(ids, mode=mode)
     if rules == W.ARITH_RULES:
         vals, inter = ev.readback_nats(ids)
         out = list(zip(vals, inter))
@@ -178,3 +178,32 @@ def test_jit_missing_nvrtc_falls_back_to_the_general_kernel(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
     assert out.returncode == 0, out.stderr
     assert out.stdout.startswith("[63, 304] -1 0 NVRTC"), out.stdout
+
+
+def tree_nets(seed: int, count: int, depth: int) -> list[str]:
+    from tests.test_oracle import tree_cases
+    nets = []
+    for t in tree_cases(seed=seed, count=count, depth=depth):
+        tt = W.tree_text(t)
+        nets += [f"< r | Mirror(r) = {tt} >", f"< r | Leaves(r) = {tt} >", f"< p, q | Copy(p, q) = {tt} >",
+                 f"< | Drop = {tt} >", f"< r | Left(r) = {tt} >", f"< r | Swap(r) = {tt} >",
+                 f"< r | Leaves(r) = x, Copy(x, y) = {tt}, Drop = y >",
+                 f"< r | Swap(r) = x, Mirror(x) = y, Mirror(y) = {tt} >"]
+    return nets
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("free_nets", [False, True])
+def test_jit_tree_rules_equal_the_oracle(orc, free_nets):
+    # a rule set with arity-two constructors: its rules of at most two new
+    # agents get their own code, the others (Mirror, Leaves, Copy of a node)
+    # run the general code in the same kernel
+    nets = tree_nets(seed=7, count=48, depth=9)
+    exp = orc.run(W.TREE_RULES, nets)
+    caps = dict(max_agents=1 << 22, max_vars=1 << 22, max_pairs=1 << 19, max_nets=512)
+    for jit, mode in ((True, "async"), (False, "async"), (False, "persistent")):
+        got, hist, info = run_async(nets, W.TREE_RULES, jit, free_nets, mode=mode, **caps)
+        assert info["state"] == (1 if jit else 0), info
+        for net, (text, n), o in zip(nets, got, exp):
+            assert o["status"] == "ok"
+            assert (text, n) == (o["result"], o["interactions"]), (mode, net)

@@ -338,3 +338,72 @@ def test_lsystem_bruteforce_all_orders(oracle, n):
     (text, _), = bf["finals"]
     r = oracle.run(W.LSYS_RULES, [net])[0]
     assert r["result"] == text and r["interactions"] == bf["min"] == lsys_counts(n)[0]
+
+
+# --- binary trees (a second rule set with arity-two constructors) -----------
+# Closed forms from the rules: a walker meets every constructor of the tree
+# once (nodes + leaves interactions); Leaves also adds, at each node, the
+# left subtree's count into the right's (Add consumes its S^k Z: k + 1
+# interactions); Left drops the right subtree; Swap touches the root only.
+
+def t_nodes(t):
+    return 0 if t is None else 1 + t_nodes(t[0]) + t_nodes(t[1])
+
+
+def t_leaves(t):
+    return 1 if t is None else t_leaves(t[0]) + t_leaves(t[1])
+
+
+def t_mirror(t):
+    return None if t is None else (t_mirror(t[1]), t_mirror(t[0]))
+
+
+def t_add_cost(t):
+    return 0 if t is None else t_leaves(t[0]) + 1 + t_add_cost(t[0]) + t_add_cost(t[1])
+
+
+def tree_cases(seed=20240607, count=40, depth=6):
+    import random
+    rng = random.Random(seed)
+    trees = [None, (None, None), ((None, None), None)]
+    while len(trees) < count:
+        trees.append(W.random_tree(rng, depth))
+    return trees
+
+
+def test_tree_walkers_values_and_counts(oracle):
+    trees = tree_cases()
+    nets, want = [], []
+    for t in trees:
+        tt, agents = W.tree_text(t), t_nodes(t) + t_leaves(t)
+        nets.append(f"< r | Mirror(r) = {tt} >")
+        want.append((W.tree_text(t_mirror(t)), agents))
+        nets.append(f"< r | Leaves(r) = {tt} >")
+        want.append((W.numeral(t_leaves(t)), agents + t_add_cost(t)))
+        nets.append(f"< p, q | Copy(p, q) = {tt} >")
+        want.append((tt + ", " + tt, agents))
+        nets.append(f"< | Drop = {tt} >")
+        want.append(("", agents))
+        nets.append(f"< r | Left(r) = {tt} >")
+        want.append(("Leaf" if t is None else W.tree_text(t[0]),
+                     1 if t is None else 1 + t_nodes(t[1]) + t_leaves(t[1])))
+        nets.append(f"< r | Swap(r) = {tt} >")
+        want.append(("Leaf" if t is None else W.tree_text((t[1], t[0])), 1))
+        nets.append(f"< r | Mirror(r) = x, Mirror(x) = {tt} >")
+        want.append((tt, 2 * agents))
+    res = oracle.run(W.TREE_RULES, nets)
+    for net, r, (text, n) in zip(nets, res, want):
+        assert r["status"] == "ok", net
+        assert (r["result"], r["interactions"]) == (text, n), net
+        assert r["residual_agents"] == 0
+
+
+@pytest.mark.parametrize("net", ["< r | Leaves(r) = Node(Node(Leaf, Leaf), Leaf) >",
+                                 "< p, q | Copy(p, q) = Node(Leaf, Node(Leaf, Leaf)) >",
+                                 "< r | Swap(r) = x, Mirror(x) = Node(Node(Leaf, Leaf), Leaf) >"])
+def test_tree_bruteforce_all_orders(oracle, net):
+    bf = bruteforce.explore(W.TREE_RULES, net)
+    assert bf["consistent"] and bf["min"] == bf["max"] and len(bf["finals"]) == 1
+    (text, _), = bf["finals"]
+    r = oracle.run(W.TREE_RULES, [net])[0]
+    assert r["result"] == text and r["interactions"] == bf["min"]

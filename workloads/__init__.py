@@ -75,6 +75,42 @@ Dup(a, b) = S(x) -> Dup(p, q) = x, a = S(p), b = S(q);
 
 LSYS_RULE_NAMES = ["SymA><Z", "SymA><S", "SymB><Z", "SymB><S", "Dup><Z", "Dup><S"]
 
+# Binary trees (Leaf, Node(a, b)) walked by agents that mirror, count the
+# leaves of, copy, drop, take the left subtree of, or swap the children of a
+# tree: a second rule set, with arity-two constructors, for the kernel
+# compiled per rule set (the paper's examples are numerals; these rules are
+# ours).  Every rule consumes one constructor, so every net terminates.
+TREE_RULES = """\
+Mirror(r) = Leaf -> r = Leaf;
+Mirror(r) = Node(a, b) -> r = Node(y, x), Mirror(x) = a, Mirror(y) = b;
+Leaves(r) = Leaf -> r = S(Z);
+Leaves(r) = Node(a, b) -> Leaves(x) = a, Leaves(y) = b, Add(y, r) = x;
+Drop = Leaf -> ;
+Drop = Node(a, b) -> Drop = a, Drop = b;
+Copy(p, q) = Leaf -> p = Leaf, q = Leaf;
+Copy(p, q) = Node(a, b) -> Copy(a1, a2) = a, Copy(b1, b2) = b, p = Node(a1, b1), q = Node(a2, b2);
+Left(r) = Leaf -> r = Leaf;
+Left(r) = Node(a, b) -> r = a, Drop = b;
+Swap(r) = Leaf -> r = Leaf;
+Swap(r) = Node(a, b) -> r = Node(b, a);
+Add(y, r) = Z -> r = y;
+Add(y, r) = S(x) -> Add(y, w) = x, r = S(w);
+"""
+
+
+def random_tree(rng, depth: int):
+    """A random binary tree of at most `depth` levels: None is a leaf, a
+    pair (left, right) a node."""
+    if depth == 0 or rng.random() < 0.3:
+        return None
+    return (random_tree(rng, depth - 1), random_tree(rng, depth - 1))
+
+
+def tree_text(t) -> str:
+    if t is None:
+        return "Leaf"
+    return f"Node({tree_text(t[0])}, {tree_text(t[1])})"
+
 # Rule names in file order (R1..R18), for per-rule histograms.
 ARITH_RULE_NAMES = [
     "Add><Z", "Add><S", "Dup><Z", "Dup><S", "Era><Z", "Era><S",
