@@ -241,9 +241,8 @@ bool jit_async(const Template* t, size_t n, bool track, const std::string& arch,
   const std::string path = dir.empty() ? std::string() : dir + "/" + key + ".cubin";
   std::string name;
   std::vector<char> cubin;
-  if (!path.empty() && read_cached(path, &name, &cubin)) {
-    out->from_disk = true;
-  } else {
+  // NVRTC: the cubin of the generated source, written to the disk cache
+  auto compile = [&]() -> bool {
     if (!nv.ok) {
       *err = nv.why;
       return false;
@@ -291,10 +290,23 @@ bool jit_async(const Template* t, size_t n, bool track, const std::string& arch,
       return false;
     }
     if (!path.empty()) write_cached(dir, path, name, cubin);
+    return true;
+  };
+  if (!path.empty() && read_cached(path, &name, &cubin)) {
+    out->from_disk = true;
+  } else if (!compile()) {
+    return false;
   }
   Loaded L;
   if (load) {
     cudaError_t e = cudaLibraryLoadData(&L.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess && out->from_disk) {
+      // a damaged cache file: compile again and replace it
+      out->from_disk = false;
+      remove(path.c_str());
+      if (!compile()) return false;
+      e = cudaLibraryLoadData(&L.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    }
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&L.kern, L.lib, name.c_str());
     if (e != cudaSuccess) {
       if (L.lib) cudaLibraryUnload(L.lib);

@@ -207,3 +207,27 @@ def test_jit_tree_rules_equal_the_oracle(orc, free_nets):
         for net, (text, n), o in zip(nets, got, exp):
             assert o["status"] == "ok"
             assert (text, n) == (o["result"], o["interactions"]), (mode, net)
+
+
+@pytest.mark.gpu
+def test_jit_damaged_cache_file_is_rebuilt(tmp_path):
+    # a cached cubin that no longer loads is compiled again and replaced
+    code = ("import workloads as W\n"
+            "from paper_1404_0076_gb300 import Evaluator\n"
+            "ev = Evaluator(device=0, max_agents=1 << 20, max_vars=1 << 20, max_pairs=1 << 16, max_nets=64)\n"
+            "ev.load_rules(W.ARITH_RULES)\n"
+            "ids = ev.load_nets([W.mul_net(5, 6)])\n"
+            "ev.reduce(ids, mode='async')\n"
+            "print(ev.readback_nats(ids)[0][0], ev.jit_info()['state'], ev.jit_info()['source'])\n")
+    env = dict(os.environ, INET_JIT_CACHE=str(tmp_path))
+    run = lambda: subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                                 timeout=300, env=env)
+    out = run()
+    assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1"], (out.stdout, out.stderr)
+    files = list(tmp_path.glob("*.cubin"))
+    assert len(files) == 1
+    head = files[0].read_bytes().split(b"\n", 1)[0]
+    files[0].write_bytes(head + b"\n" + b"not a cubin" * 16)
+    out = run()
+    assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1"], (out.stdout, out.stderr)
+    assert files[0].read_bytes()[len(head) + 1:] != b"not a cubin" * 16
