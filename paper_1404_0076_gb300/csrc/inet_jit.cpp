@@ -299,17 +299,28 @@ bool jit_async(const Template* t, size_t n, bool track, const std::string& arch,
   }
   Loaded L;
   if (load) {
-    cudaError_t e = cudaLibraryLoadData(&L.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    // the image is checked when it is loaded or, with lazy loading, when the
+    // kernel is looked up
+    auto load_kernel = [&]() -> cudaError_t {
+      L = Loaded{};
+      cudaError_t e = cudaLibraryLoadData(&L.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+      if (e == cudaSuccess) e = cudaLibraryGetKernel(&L.kern, L.lib, name.c_str());
+      if (e != cudaSuccess) {
+        if (L.lib) cudaLibraryUnload(L.lib);
+        L = Loaded{};
+        cudaGetLastError();  // the failure is reported here, not to the context's next call
+      }
+      return e;
+    };
+    cudaError_t e = load_kernel();
     if (e != cudaSuccess && out->from_disk) {
       // a damaged cache file: compile again and replace it
       out->from_disk = false;
       remove(path.c_str());
       if (!compile()) return false;
-      e = cudaLibraryLoadData(&L.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+      e = load_kernel();
     }
-    if (e == cudaSuccess) e = cudaLibraryGetKernel(&L.kern, L.lib, name.c_str());
     if (e != cudaSuccess) {
-      if (L.lib) cudaLibraryUnload(L.lib);
       *err = std::string("loading the specialised kernel failed: ") + cudaGetErrorString(e);
       return false;
     }

@@ -218,16 +218,17 @@ def test_jit_damaged_cache_file_is_rebuilt(tmp_path):
             "ev.load_rules(W.ARITH_RULES)\n"
             "ids = ev.load_nets([W.mul_net(5, 6)])\n"
             "ev.reduce(ids, mode='async')\n"
-            "print(ev.readback_nats(ids)[0][0], ev.jit_info()['state'], ev.jit_info()['source'])\n")
+            "print(ev.readback_nats(ids)[0][0], ev.jit_info()['state'], ev.jit_info()['source'], "
+            "repr(ev.jit_info()['msg']))\n")
     env = dict(os.environ, INET_JIT_CACHE=str(tmp_path))
     run = lambda: subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                                  timeout=300, env=env)
     out = run()
-    assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1"], (out.stdout, out.stderr)
+    assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1", "''"], (out.stdout, out.stderr)
     files = list(tmp_path.glob("*.cubin"))
     assert len(files) == 1
     head = files[0].read_bytes().split(b"\n", 1)[0]
     files[0].write_bytes(head + b"\n" + b"not a cubin" * 16)
     out = run()
-    assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1"], (out.stdout, out.stderr)
+    assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1", "''"], (out.stdout, out.stderr)
     assert files[0].read_bytes()[len(head) + 1:] != b"not a cubin" * 16
