@@ -560,12 +560,20 @@ __device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, W
 // agents, 11.0 ms up to three, 11.2 ms with every rule; only up to one
 // leaves the Add chains out and gives no gain).
 constexpr int kSpecialisedMaxNew = 2;
+// At most this many rules get their own code (the first in rule-table
+// order): every one adds to the run-time compile (about 0.4 s each) and to
+// the kernel's code.
+constexpr int kSpecialisedMaxRules = 32;
 // Bit I set: rule I has its own code.
 template <class Rules>
 __host__ __device__ constexpr unsigned long long spec_mask() {
   unsigned long long m = 0;
-  for (int i = 0; i < Rules::kN; i++)
-    if (Rules::kT[i].n_new <= kSpecialisedMaxNew) m |= 1ull << i;
+  int k = 0;
+  for (int i = 0; i < Rules::kN && k < kSpecialisedMaxRules; i++)
+    if (Rules::kT[i].n_new <= kSpecialisedMaxNew) {
+      m |= 1ull << i;
+      k++;
+    }
   return m;
 }
 template <class Rules, int I>

@@ -232,3 +232,39 @@ def test_jit_damaged_cache_file_is_rebuilt(tmp_path):
     out = run()
     assert out.returncode == 0 and out.stdout.split() == ["30", "1", "1", "''"], (out.stdout, out.stderr)
     assert files[0].read_bytes()[len(head) + 1:] != b"not a cubin" * 16
+
+
+def ring_rules(k: int = 32) -> str:
+    """2k rules (64 for k = 32, the most a rule set may hold): C_i passes a
+    numeral on as C_(i+1 mod k), one S at a time."""
+    out = []
+    for i in range(k):
+        out.append(f"C{i}(r) = Z -> r = Z;")
+        out.append(f"C{i}(r) = S(x) -> C{(i + 1) % k}(w) = x, r = S(w);")
+    return "\n".join(out) + "\n"
+
+
+def test_jit_builds_the_largest_rule_set(capi, tmp_path, monkeypatch):
+    # 64 rules: the first 32 with two new agents or fewer get their own code
+    monkeypatch.setenv("INET_JIT_CACHE", str(tmp_path))
+    ctx = capi.inet_create(-1)
+    capi.inet_load_rules(ctx, ring_rules())
+    assert capi.inet_rule_count(ctx) == 64
+    capi.inet_jit_build(ctx, False)
+    assert capi.inet_jit_info(ctx)["source"] == 1
+    capi.inet_destroy(ctx)
+
+
+@pytest.mark.gpu
+def test_jit_largest_rule_set_equals_the_oracle(orc):
+    # chains that pass through all 64 rules, half of them with their own
+    # code and half on the general code, in one kernel
+    rules = ring_rules()
+    nets = [f"< r | C{i}(r) = {W.numeral(n)} >" for i in range(32) for n in (0, 1, 7, 40, 129)]
+    exp = orc.run(rules, nets)
+    got, hist, info = run_async(nets, rules, True, max_agents=1 << 20, max_vars=1 << 20, max_pairs=1 << 16,
+                                max_nets=256)
+    assert info["state"] == 1
+    for net, (text, n), o in zip(nets, got, exp):
+        assert (text, n) == (o["result"], o["interactions"]), net
+    assert sum(hist) == sum(o["interactions"] for o in exp)
