@@ -30,6 +30,13 @@
 // slots its warps return at the end.  The other instantiation has none of
 // that code in its loop (code the loop does not run still costs this kernel
 // time through instruction fetch and scheduling).
+//
+// Rules (a rule set known when the kernel is compiled, see inet_jit.h): the
+// library compiles k_async<kTrack, Rules> at run time for the loaded rule
+// set; a warp whose lanes all reduce one of its small rules runs that rule's
+// own straight-line code (uni_interact, rule_body), every other warp the
+// general code below it.  NoRules is the general kernel built with the
+// library.
 #pragma once
 
 #include "inet_kernels.cuh"
