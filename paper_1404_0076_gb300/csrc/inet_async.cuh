@@ -566,6 +566,126 @@ __device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, W
 // fetch than they save (2048 Mul nets: 10.9 ms with rules of up to two
 // agents, 11.0 ms up to three, 11.2 ms with every rule; only up to one
 // leaves the Add chains out and gives no gain).
+// Rule I continues as a chain of itself when one of its equations joins an
+// external port to a new agent of one of its own left-hand side's symbols:
+// Add(y, w) = x of Add(y, r) = S(x) -> Add(y, w) = x, r = S(w), where an
+// agent x in the port makes (Add', x) the next active pair, often of the
+// same rule.
+template <class Rules, int I>
+__host__ __device__ constexpr bool chain_rule() {
+  if constexpr (I < Rules::kN) {
+    constexpr Template R = Rules::kT[I];
+    for (int k = 0; k < R.n_link; k++) {
+      const int c0 = R.link[k][0], c1 = R.link[k][1];
+      const bool e0 = c0 < kValNew, e1 = c1 < kValNew;
+      const bool n0 = c0 >= kValNew && c0 < kValFresh, n1 = c1 >= kValNew && c1 < kValFresh;
+      if ((e0 && n1) || (n0 && e1)) {
+        const int lab = R.lab[(e0 ? c1 : c0) - kValNew];
+        if (lab == R.lhs[0] || lab == R.lhs[1]) return true;
+      }
+    }
+  }
+  return false;
+}
+
+constexpr int kLoneMax = 32;  // interactions of one lone run before the warp's loop resumes
+
+// A warp in which one lane holds a pair (no lane waits for a ticket, and the
+// queue was empty when the warp last looked), of a rule that continues as a
+// chain of itself: the lane runs up to kLoneMax interactions of that rule on
+// its own, without the warp's loop between them.  Each leaves exactly one
+// new pair, the chain's next, so nothing is handed on and the count of pairs
+// in flight does not change.  The run stops when an interaction leaves no
+// pair or several (returned as after any step, W.out filled), when the next
+// pair is of another rule or its slots are not on the warp's stacks (it is
+// then the lane's next pair), or after kLoneMax interactions.  Slots come
+// from and return to the warp's stacks, names freed while linking too;
+// counters per interaction as in the warp's step.  (Loading the next
+// pair's records before an interaction's fence and exchanges returned, or
+// handing the records this run loaded back to the warp's loop, was slower.)
+template <bool kTrack, class Rules, int I>
+__device__ __forceinline__ uint32_t lone_chain(const Dev& d, const int16_t* tab, uint32_t* hist, WarpMem& W,
+                                               WarpStacks& S, bool valid, uint32_t a, uint32_t b, int4 ra, int4 rb,
+                                               uint32_t net, long long& live) {
+  constexpr Template R = Rules::kT[I];
+  constexpr uint32_t NN = R.n_new, NF = R.n_fresh;
+  constexpr uint32_t NA = NN > 2 ? NN - 2 : 0u, FA = NN < 2 ? 2 - NN : 0u;
+  const int lane = threadIdx.x & 31;
+  Ctrl* c = d.ctrl;
+  const unsigned vm = __ballot_sync(kFull, valid);
+  const int src = vm ? __ffs(vm) - 1 : 0;
+  uint32_t np = 0;
+  int ac = S.ac, vc = S.vc;
+  long long dl = 0;
+  if (valid) {
+    for (int it = 0;; it++) {
+      np = rule_body<kTrack, Rules, I>(d, W, ra, rb, a, b, net, 0u, 0u, NA, NF, (uint32_t)ac - NA,
+                                       (uint32_t)vc - NF, 0ull, 0u, 0ull, 0ull, 0u, 0ull, lane, valid);
+      ac -= (int)NA;
+      vc -= (int)NF;
+#pragma unroll
+      for (uint32_t f = 0; f < FA; f++) {
+        const uint32_t slot = (NN == 0 && f == 0) ? a : b;
+        if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
+        if (ac < kAStack) {
+          W.astk[ac++] = slot;
+        } else {
+          const unsigned long long tp = atomicAdd(&c->a_tail, 1ull);
+          __stcg(d.afree + tp % d.cap_agents, slot);
+        }
+      }
+      dl += (long long)NA - (long long)FA;
+      // names freed while linking: this lane is the only user of the warp's stacks
+      const int nst = min(W.vstage_n, kVStageW);
+      for (int j = 0; j < nst; j++) {
+        if (vc < kVStack) {
+          W.vstk[vc++] = W.vstage[j];
+        } else {
+          const unsigned long long tp = atomicAdd(&c->v_tail, 1ull);
+          __stcg(d.vfree + tp % d.cap_vars, W.vstage[j]);
+        }
+      }
+      W.vstage_n = 0;
+      if (!valid) break;
+      count_interaction<kTrack>(d, hist, net, R.rule, np, NN);
+      if (np != 1 || it + 1 >= kLoneMax) break;
+      // the one new pair: the chain's next if it is of rule I again
+      const Pair p = W.out[0][lane];
+      if (p.a >= d.cap_agents || p.b >= d.cap_agents) break;
+      const int4 pra = ld_node(d.node + p.a), prb = ld_node(d.node + p.b);
+      const uint32_t la = (uint32_t)pra.x & 0xFFu, lb = (uint32_t)prb.x & 0xFFu;
+      const int e = (la < d.n_labels && lb < d.n_labels) ? tab[la * d.n_labels + lb] : -1;
+      if (e < 0 || ((uint32_t)e >> 1) != (uint32_t)I || ac < (int)NA || vc < (int)NF) break;
+      if (e & 1) {
+        ra = prb;
+        rb = pra;
+        a = p.b;
+        b = p.a;
+      } else {
+        ra = pra;
+        rb = prb;
+        a = p.a;
+        b = p.b;
+      }
+      net = (uint32_t)ra.x >> 8;
+      if (net >= d.max_nets) break;  // left to the warp's step, which reports it
+    }
+  }
+  __syncwarp();
+  S.ac = __shfl_sync(kFull, ac, src);
+  S.vc = __shfl_sync(kFull, vc, src);
+  const long long dls = __shfl_sync(kFull, dl, src);
+  if (lane == 0) live += dls;
+  return valid ? np : 0u;
+}
+
+// The warp's stacks hold the slots of one interaction of rule I.
+template <class Rules, int I>
+__device__ __forceinline__ bool lone_slots(const WarpStacks& S) {
+  constexpr uint32_t NN = Rules::kT[I].n_new;
+  return S.ac >= (int)(NN > 2 ? NN - 2 : 0) && S.vc >= (int)Rules::kT[I].n_fresh;
+}
+
 constexpr int kSpecialisedMaxNew = 2;
 // At most this many rules get their own code (the first in rule-table
 // order): every one adds to the run-time compile (about 0.4 s each) and to
@@ -589,8 +709,13 @@ __host__ __device__ constexpr bool specialised() {
 }
 #define INET_UNI_CASE(I)                                                                                   \
   case I:                                                                                                  \
-    if constexpr (specialised<Rules, I>())                                                                 \
+    if constexpr (specialised<Rules, I>()) {                                                               \
+      if constexpr (chain_rule<Rules, I>()) {                                                              \
+        if (lone && lone_slots<Rules, I>(S))                                                               \
+          return lone_chain<kTrack, Rules, I>(d, tab, hist, W, S, valid, a, b, ra, rb, net, live);         \
+      }                                                                                                    \
       return uni_interact<kTrack, Rules, I>(d, hist, W, S, valid, vmask, a, b, ra, rb, net, live);         \
+    }                                                                                                      \
     break;
 
 // One interaction per lane whose `valid` is set (warp-collective).  The new
@@ -604,7 +729,7 @@ template <bool kTrack, class Rules>
 __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl* tmpl, const int16_t* tab,
                                                    uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
                                                    uint32_t a, uint32_t b, long long& live, bool pre,
-                                                   int4 pra, int4 prb) {
+                                                   int4 pra, int4 prb, bool lone) {
   const int lane = threadIdx.x & 31;
   Ctrl* c = d.ctrl;
   uint32_t net = 0, ti = 0;
@@ -824,6 +949,7 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
   uint32_t nap = 0;
   bool stop = false, finished = false, check_now = false;
   bool pre = false;
+  bool qseen = false;  // the queue held pairs when this warp last looked
   int4 pra = make_int4(0, 0, 0, 0), prb = pra;
   unsigned long long t_start = 0;
   if (lane == 0) {
@@ -862,11 +988,12 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
     const unsigned busy = __ballot_sync(kFull, have);
     if (want && (!busy || (it & 7) == 0)) {
       unsigned long long base = 0;
-      uint32_t k = 0;
+      uint32_t k = 0, qs = 0;
       if (lane == 0) {
         unsigned long long qh, qt;
         asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(qh), "=l"(qt) : "l"(&c->q_head) : "memory");
         const unsigned long long backlog = qt > qh ? qt - qh : 0ull;
+        qs = backlog ? 1u : 0u;
         const bool deep = backlog > total_warps;
         if (backlog && (!busy || deep)) {
           k = (uint32_t)min(min((unsigned long long)__popc(want), backlog), deep ? 32ull : 1ull);
@@ -874,6 +1001,7 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
         }
       }
       k = __shfl_sync(kFull, k, 0);
+      qseen = __shfl_sync(kFull, qs, 0) != 0;
       if (k) {
         unsigned long long bm = 0;
         if (lane == 0) bm = base % cap;
@@ -912,7 +1040,12 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
       continue;
     }
     nap = 0;
-    const uint32_t np = async_interact<kTrack, Rules>(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb);
+    // one lane holds a pair, no lane waits for a ticket, the queue was empty
+    // when the warp last looked: a chain may run alone (queued work is left
+    // to the warp's loop, whose idle lanes claim it)
+    const bool lone = !qseen && __popc(act) == 1 && __ballot_sync(kFull, ticket != kNoTicket) == 0;
+    const uint32_t np = async_interact<kTrack, Rules>(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb,
+                                                      lone);
     // keep the first new pair and start loading its records now, so the
     // load overlaps the rest of this iteration
     const bool had = have;

@@ -198,9 +198,11 @@ std::string jit_source(const Template* t, size_t n) {
       s += buf;
     }
     for (int k = 0; k < kMaxLink; k++) {
-      snprintf(buf, sizeof buf, "{%u, %u}%s", r.link[k][0], r.link[k][1], k + 1 < kMaxLink ? ", " : "}, {0}},\n");
+      snprintf(buf, sizeof buf, "{%u, %u}%s", r.link[k][0], r.link[k][1], k + 1 < kMaxLink ? ", " : "}, ");
       s += buf;
     }
+    snprintf(buf, sizeof buf, "{%u, %u}, {0}},\n", r.lhs[0], r.lhs[1]);
+    s += buf;
   }
   s += "  };\n};\n}  // namespace inet\n";
   return s;

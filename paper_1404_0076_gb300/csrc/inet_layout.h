@@ -85,7 +85,8 @@ struct alignas(16) Template {
   uint8_t lab[kMaxNew];        // labels of the new agents
   uint8_t src[kMaxNew][3];     // value codes written to their auxiliary ports
   uint8_t link[kMaxLink][2];   // value codes of each equation t = u to link
-  uint8_t pad[12];
+  uint8_t lhs[2];              // labels of the left-hand side's agents (alpha, beta)
+  uint8_t pad[10];
 };
 static_assert(sizeof(Template) == 64, "template is 64 bytes");
 

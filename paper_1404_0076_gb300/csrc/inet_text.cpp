@@ -320,6 +320,8 @@ int compile_one(const std::string& src, const std::vector<Tok>& toks, Reader& rd
   tab[(size_t)a * L + b] = (int16_t)(idx << 1);
   tab[(size_t)b * L + a] = (int16_t)((idx << 1) | 1);
   out.table.swap(tab);
+  t.lhs[0] = (uint8_t)a;
+  t.lhs[1] = (uint8_t)b;
   out.tmpl.push_back(t);
   out.rule_names.push_back(out.labels[(size_t)a] + "><" + out.labels[(size_t)b]);
   (void)src;
