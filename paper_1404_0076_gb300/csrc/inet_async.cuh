@@ -484,88 +484,6 @@ __device__ __forceinline__ uint32_t rule_body(const Dev& d, WarpMem& W, const in
   return np;
 }
 
-// A warp whose valid lanes all reduce rule I of a specialised rule set (the
-// common case: one lane alone on a chain, or a batch of like pairs): the
-// whole step with that rule's template as a constant.  Every lane needs the
-// same slots, so a lane's offsets among the warp's needs are its rank among
-// the valid lanes times the rule's counts, with no scan.
-template <bool kTrack, class Rules, int I>
-__device__ __forceinline__ uint32_t uni_interact(const Dev& d, uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
-                                                 unsigned vmask, uint32_t a, uint32_t b, const int4& ra,
-                                                 const int4& rb, uint32_t net, long long& live) {
-  constexpr Template R = Rules::kT[I];
-  constexpr uint32_t NN = R.n_new, NF = R.n_fresh;
-  constexpr uint32_t NA = NN > 2 ? NN - 2 : 0u, FA = NN < 2 ? 2 - NN : 0u;
-  const int lane = threadIdx.x & 31;
-  Ctrl* c = d.ctrl;
-  const uint32_t nvl = __popc(vmask), rank = __popc(vmask & lanemask_lt());
-  const uint32_t Ka = nvl * NA, Kv = nvl * NF, Fa = nvl * FA;
-  const uint32_t oa = rank * NA, ov = rank * NF, of = rank * FA;
-  const uint32_t ta = min((uint32_t)S.ac, Ka), tv = min((uint32_t)S.vc, Kv);
-  const uint32_t abase = (uint32_t)S.ac - ta, vbase = (uint32_t)S.vc - tv;
-  const uint32_t ga = Ka - ta, gv = Kv - tv;
-  const uint32_t gra = ga ? (uint32_t)kRefill : 0u, grv = gv ? (uint32_t)kRefill : 0u;
-  unsigned long long arb = 0, abb = 0, vrb = 0, vbb = 0;
-  uint32_t aav = 0, vav = 0;
-  if (ga | gv) {
-    uint32_t ok = 1;
-    if (lane == 0) {
-      ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &arb, &aav, &abb) ? 1u : 0u;
-      ok &= pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &vrb, &vav, &vbb) ? 1u : 0u;
-      if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
-    }
-    if (!__shfl_sync(kFull, ok, 0)) return 0u;  // fatal: the loop stops
-    arb = __shfl_sync(kFull, arb, 0);
-    abb = __shfl_sync(kFull, abb, 0);
-    aav = __shfl_sync(kFull, aav, 0);
-    vrb = __shfl_sync(kFull, vrb, 0);
-    vbb = __shfl_sync(kFull, vbb, 0);
-    vav = __shfl_sync(kFull, vav, 0);
-  }
-  if (lane == 0) live += (long long)Ka - (long long)Fa;
-  const bool frees = valid;  // counted in Fa: freed even if the step fails below
-  uint32_t np = 0;
-  if (valid)
-    np = rule_body<kTrack, Rules, I>(d, W, ra, rb, a, b, net, oa, ov, ta, tv, abase, vbase, arb, aav, abb, vrb, vav,
-                                     vbb, lane, valid);
-  __syncwarp();  // every taken stack entry has been read
-  if (gra | grv) {
-    if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, arb, aav, abb, ga + lane);
-    if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, gv + lane);
-  }
-  const uint32_t atop = abase + gra;
-  const uint32_t keep = min((uint32_t)kAStack - atop, Fa);
-  if (FA && Fa) {
-    unsigned long long over = 0;
-    if (Fa > keep) {
-      if (lane == 0) over = atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep));
-      over = __shfl_sync(kFull, over, 0);
-    }
-    if (frees) {
-#pragma unroll
-      for (uint32_t f = 0; f < FA; f++) {
-        const uint32_t slot = (NN == 0 && f == 0) ? a : b;
-        const uint32_t k = of + f;
-        if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
-        if (k < keep) W.astk[atop + k] = slot;
-        else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
-      }
-    }
-  }
-  S.ac = (int)(atop + keep);
-  S.vc = (int)(vbase + grv);
-  flush_vstage(d, W, S, lane);
-  if (valid) count_interaction<kTrack>(d, hist, net, R.rule, np, NN);
-  return valid ? np : 0u;
-}
-
-// Rule I of a specialised rule set, when the rule set has one and I's
-// right-hand side has at most two agents (it reuses the pair's two slots:
-// the rules that carry chains, Add(y, r) = S(x) and the like).  Larger
-// rules stay on the general code: their own copies cost more in instruction
-// fetch than they save (2048 Mul nets: 10.9 ms with rules of up to two
-// agents, 11.0 ms up to three, 11.2 ms with every rule; only up to one
-// leaves the Add chains out and gives no gain).
 // Rule I continues as a chain of itself when one of its equations joins an
 // external port to a new agent of one of its own left-hand side's symbols:
 // Add(y, w) = x of Add(y, r) = S(x) -> Add(y, w) = x, r = S(w), where an
@@ -589,6 +507,133 @@ __host__ __device__ constexpr bool chain_rule() {
 }
 
 constexpr int kLoneMax = 32;  // interactions of one lone run before the warp's loop resumes
+
+// A warp whose valid lanes all reduce rule I of a specialised rule set (the
+// common case: one lane alone on a chain, or a batch of like pairs): the
+// whole step with that rule's template as a constant.  Every lane needs the
+// same slots, so a lane's offsets among the warp's needs are its rank among
+// the valid lanes times the rule's counts, with no scan.
+//
+// Uniform runs: when `quiet` (no lane waits for a ticket and the queue was
+// empty when the warp last looked), the rule continues as a chain of itself
+// and every valid lane's step left exactly one new pair, of rule I again,
+// the warp steps again at once with those pairs, without its loop between
+// (up to kLoneMax steps): nothing is handed on, the count of pairs in flight
+// does not change.  A warp with one valid lane leaves this to lone_chain.
+template <bool kTrack, class Rules, int I>
+__device__ __forceinline__ uint32_t uni_interact(const Dev& d, const int16_t* tab, uint32_t* hist, WarpMem& W,
+                                                 WarpStacks& S, bool valid, unsigned vmask, uint32_t a, uint32_t b,
+                                                 int4 ra, int4 rb, uint32_t net, long long& live, bool quiet) {
+  constexpr Template R = Rules::kT[I];
+  constexpr uint32_t NN = R.n_new, NF = R.n_fresh;
+  constexpr uint32_t NA = NN > 2 ? NN - 2 : 0u, FA = NN < 2 ? 2 - NN : 0u;
+  const int lane = threadIdx.x & 31;
+  Ctrl* c = d.ctrl;
+  const uint32_t nvl = __popc(vmask), rank = __popc(vmask & lanemask_lt());
+  const uint32_t Ka = nvl * NA, Kv = nvl * NF, Fa = nvl * FA;
+  const uint32_t oa = rank * NA, ov = rank * NF, of = rank * FA;
+  uint32_t np = 0;
+  for (int it = 0;; it++) {
+    const uint32_t ta = min((uint32_t)S.ac, Ka), tv = min((uint32_t)S.vc, Kv);
+    const uint32_t abase = (uint32_t)S.ac - ta, vbase = (uint32_t)S.vc - tv;
+    const uint32_t ga = Ka - ta, gv = Kv - tv;
+    const uint32_t gra = ga ? (uint32_t)kRefill : 0u, grv = gv ? (uint32_t)kRefill : 0u;
+    unsigned long long arb = 0, abb = 0, vrb = 0, vbb = 0;
+    uint32_t aav = 0, vav = 0;
+    if (ga | gv) {
+      uint32_t ok = 1;
+      if (lane == 0) {
+        ok = pool_pop(&c->a_head, &c->a_pub, &c->a_bump, d.cap_agents, ga + gra, &arb, &aav, &abb) ? 1u : 0u;
+        ok &= pool_pop(&c->v_head, &c->v_pub, &c->v_bump, d.cap_vars, gv + grv, &vrb, &vav, &vbb) ? 1u : 0u;
+        if (!ok) set_error(c, INET_ERR_ARENA_FULL, 0);
+      }
+      if (!__shfl_sync(kFull, ok, 0)) return 0u;  // fatal: the loop stops
+      arb = __shfl_sync(kFull, arb, 0);
+      abb = __shfl_sync(kFull, abb, 0);
+      aav = __shfl_sync(kFull, aav, 0);
+      vrb = __shfl_sync(kFull, vrb, 0);
+      vbb = __shfl_sync(kFull, vbb, 0);
+      vav = __shfl_sync(kFull, vav, 0);
+    }
+    if (lane == 0) live += (long long)Ka - (long long)Fa;
+    const bool frees = valid;  // counted in Fa: freed even if the step fails below
+    np = 0;
+    if (valid)
+      np = rule_body<kTrack, Rules, I>(d, W, ra, rb, a, b, net, oa, ov, ta, tv, abase, vbase, arb, aav, abb, vrb,
+                                       vav, vbb, lane, valid);
+    __syncwarp();  // every taken stack entry has been read
+    if (gra | grv) {
+      if ((uint32_t)lane < gra) W.astk[abase + lane] = pool_slot(d.afree, d.cap_agents, arb, aav, abb, ga + lane);
+      if ((uint32_t)lane < grv) W.vstk[vbase + lane] = pool_slot(d.vfree, d.cap_vars, vrb, vav, vbb, gv + lane);
+    }
+    const uint32_t atop = abase + gra;
+    const uint32_t keep = min((uint32_t)kAStack - atop, Fa);
+    if (FA && Fa) {
+      unsigned long long over = 0;
+      if (Fa > keep) {
+        if (lane == 0) over = atomicAdd(&c->a_tail, (unsigned long long)(Fa - keep));
+        over = __shfl_sync(kFull, over, 0);
+      }
+      if (frees) {
+#pragma unroll
+        for (uint32_t f = 0; f < FA; f++) {
+          const uint32_t slot = (NN == 0 && f == 0) ? a : b;
+          const uint32_t k = of + f;
+          if constexpr (kTrack) __stcg(&d.node[slot].head, kFreeHead);
+          if (k < keep) W.astk[atop + k] = slot;
+          else __stcg(d.afree + (over + (k - keep)) % d.cap_agents, slot);
+        }
+      }
+    }
+    S.ac = (int)(atop + keep);
+    S.vc = (int)(vbase + grv);
+    flush_vstage(d, W, S, lane);
+    if (valid) count_interaction<kTrack>(d, hist, net, R.rule, np, NN);
+    if constexpr (!chain_rule<Rules, I>()) {
+      break;
+    } else {
+      // every lane's chain goes on with another pair of rule I: the warp
+      // steps again without its loop (the records read here are wasted when
+      // some lane's next pair is of another rule: once at the end of a chain)
+      if (!quiet || nvl == 1 || it + 1 >= kLoneMax || !__all_sync(kFull, !valid || np == 1)) break;
+      bool ok = true;
+      if (valid) {
+        ok = false;
+        const Pair p = W.out[0][lane];
+        if (p.a < d.cap_agents && p.b < d.cap_agents) {
+          const int4 pra = ld_node(d.node + p.a), prb = ld_node(d.node + p.b);
+          const uint32_t la = (uint32_t)pra.x & 0xFFu, lb = (uint32_t)prb.x & 0xFFu;
+          const int e = (la < d.n_labels && lb < d.n_labels) ? tab[la * d.n_labels + lb] : -1;
+          if (e >= 0 && ((uint32_t)e >> 1) == (uint32_t)I) {
+            if (e & 1) {
+              ra = prb;
+              rb = pra;
+              a = p.b;
+              b = p.a;
+            } else {
+              ra = pra;
+              rb = prb;
+              a = p.a;
+              b = p.b;
+            }
+            net = (uint32_t)ra.x >> 8;
+            ok = net < d.max_nets;
+          }
+        }
+      }
+      if (!__all_sync(kFull, ok)) break;
+    }
+  }
+  return valid ? np : 0u;
+}
+
+// Rule I of a specialised rule set, when the rule set has one and I's
+// right-hand side has at most two agents (it reuses the pair's two slots:
+// the rules that carry chains, Add(y, r) = S(x) and the like).  Larger
+// rules stay on the general code: their own copies cost more in instruction
+// fetch than they save (2048 Mul nets: 10.9 ms with rules of up to two
+// agents, 11.0 ms up to three, 11.2 ms with every rule; only up to one
+// leaves the Add chains out and gives no gain).
 
 // A warp in which one lane holds a pair (no lane waits for a ticket, and the
 // queue was empty when the warp last looked), of a rule that continues as a
@@ -714,7 +759,7 @@ __host__ __device__ constexpr bool specialised() {
         if (lone && lone_slots<Rules, I>(S))                                                               \
           return lone_chain<kTrack, Rules, I>(d, tab, hist, W, S, valid, a, b, ra, rb, net, live);         \
       }                                                                                                    \
-      return uni_interact<kTrack, Rules, I>(d, hist, W, S, valid, vmask, a, b, ra, rb, net, live);         \
+      return uni_interact<kTrack, Rules, I>(d, tab, hist, W, S, valid, vmask, a, b, ra, rb, net, live, quiet); \
     }                                                                                                      \
     break;
 
@@ -729,7 +774,7 @@ template <bool kTrack, class Rules>
 __device__ __forceinline__ uint32_t async_interact(const Dev& d, const AsyncTpl* tmpl, const int16_t* tab,
                                                    uint32_t* hist, WarpMem& W, WarpStacks& S, bool valid,
                                                    uint32_t a, uint32_t b, long long& live, bool pre,
-                                                   int4 pra, int4 prb, bool lone) {
+                                                   int4 pra, int4 prb, bool lone, bool quiet) {
   const int lane = threadIdx.x & 31;
   Ctrl* c = d.ctrl;
   uint32_t net = 0, ti = 0;
@@ -1040,12 +1085,13 @@ __global__ void __launch_bounds__(256, 2) k_async(Dev d) {
       continue;
     }
     nap = 0;
-    // one lane holds a pair, no lane waits for a ticket, the queue was empty
-    // when the warp last looked: a chain may run alone (queued work is left
-    // to the warp's loop, whose idle lanes claim it)
-    const bool lone = !qseen && __popc(act) == 1 && __ballot_sync(kFull, ticket != kNoTicket) == 0;
+    // no lane waits for a ticket and the queue was empty when the warp last
+    // looked: chains may run without the warp's loop (queued work is left to
+    // the loop, whose idle lanes claim it); lone: one lane holds a pair
+    const bool quiet = !qseen && __ballot_sync(kFull, ticket != kNoTicket) == 0;
+    const bool lone = quiet && __popc(act) == 1;
     const uint32_t np = async_interact<kTrack, Rules>(d, tmpl, tab, hist, W, S, have, pa, pb, live, pre, pra, prb,
-                                                      lone);
+                                                      lone, quiet);
     // keep the first new pair and start loading its records now, so the
     // load overlaps the rest of this iteration
     const bool had = have;
