@@ -506,7 +506,7 @@ __host__ __device__ constexpr bool chain_rule() {
   return false;
 }
 
-constexpr int kLoneMax = 32;  // interactions of one lone run before the warp's loop resumes
+constexpr int kLoneMax = 32;  // steps of one lone or uniform run before the warp's loop resumes
 
 // A warp whose valid lanes all reduce rule I of a specialised rule set (the
 // common case: one lane alone on a chain, or a batch of like pairs): the
