@@ -733,8 +733,9 @@ __device__ __forceinline__ bool lone_slots(const WarpStacks& S) {
 
 constexpr int kSpecialisedMaxNew = 2;
 // At most this many rules get their own code (the first in rule-table
-// order): every one adds to the run-time compile (about 0.4 s each) and to
-// the kernel's code.
+// order): every one adds to the run-time compile (up to about a second each:
+// a rule set of 64 rules compiles in about 33 s, once) and to the kernel's
+// code.
 constexpr int kSpecialisedMaxRules = 32;
 // Bit I set: rule I has its own code.
 template <class Rules>

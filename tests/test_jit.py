@@ -246,6 +246,7 @@ def ring_rules(k: int = 32) -> str:
 
 def test_jit_builds_the_largest_rule_set(capi, tmp_path, monkeypatch):
     # 64 rules: the first 32 with two new agents or fewer get their own code
+    # (about half a minute of NVRTC)
     monkeypatch.setenv("INET_JIT_CACHE", str(tmp_path))
     ctx = capi.inet_create(-1)
     capi.inet_load_rules(ctx, ring_rules())
