@@ -48,12 +48,14 @@ class Parsed:
     """A batch of nets parsed by Evaluator.parse; freed when dropped."""
 
     def __init__(self, handle):
+        # Bound now: a batch dropped at interpreter exit cannot import.
+        self._free = capi_lazy.inet_parsed_free
         self.handle = handle
         self.n = capi_lazy.inet_parsed_info(handle)[0]
 
     def __del__(self):
         if getattr(self, "handle", None):
-            capi_lazy.inet_parsed_free(self.handle)
+            self._free(self.handle)
             self.handle = None
 
 
